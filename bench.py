@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the Defrise-Clack reconstruction on GB300.
+
+One step reconstructs one volume per GPU (Eq. 12): dc_filter over every view,
+then dc_backproject.  Default workload: circle (360 views) plus a
+perpendicular 60-degree arc (136 views), 384x512 detector at 0.6 mm,
+720 x 512 planes per view, 512^3 volume, FP32 (the circle-plus-arc
+configuration of the paper's workload class), seeded 20-ellipsoid phantom
+with exact line integrals.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 is launched by torchrun: every rank reconstructs its own phantom (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "512³ DC-FBP recon ms/volume"
+UNIT = "ms/volume"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+# FP32 operations the algorithm needs per unit of work (FMA = 2), used for
+# the ALU roofline of the gather kernels (derivation in the design notes):
+#   k_bp3d    per voxel-view update: depth FMA, reciprocal, 2 FMA for (u,v),
+#             2 fraction subtractions, 3 lerps (sub+FMA), distance FMA x2,
+#             reciprocal, weight multiply, accumulate                   -> 25
+#   k_linesum per Joseph step: position FMA, fraction, lerp (sub+FMA),
+#             accumulate                                                -> 7
+#   k_bp2d    per pixel-angle pair: position FMA, fraction, two hat
+#             weights (FMA+max each), two taps (FMA each)               -> 13
+FLOPS_PER_UNIT = {"k_bp3d": 25.0, "k_linesum": 7.0, "k_bp2d": 13.0}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="circle_arc512")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- utilities
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        return json.load(open(PEAKS_FILE)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def work_units(desc, B):
+    """Algorithmic units per step: Joseph steps, pixel-angle pairs, updates."""
+    V, H, W = desc["n_views"], desc["det_rows"], desc["det_cols"]
+    n_mu, n_s = desc["n_mu"], desc["n_s"]
+    rows = sum(H if (4 * m <= n_mu or 4 * m >= 3 * n_mu) else W for m in range(n_mu))
+    return {"k_linesum": float(B) * V * rows * n_s,
+            "k_bp2d": float(B) * V * n_mu * H * W,
+            "k_bp3d": float(B) * V * desc["vol_x"] * desc["vol_y"] * desc["vol_z"]}
+
+
+# --------------------------------------------------------------- CPU oracle
+def oracle_sample(w, g_np, n_views_sample: int, n_vox_sample: int, seed: int = 0):
+    """Time the FP64 oracle on a bounded sample and scale to one volume (ms)."""
+    from oracle import oracle as orc
+    desc = w.desc_dict()
+    geom = orc.Geometry(desc, w.matrices(), w.orbit.vdl)
+    V = desc["n_views"]
+    rng = np.random.default_rng(seed)
+    views = np.sort(rng.choice(V, size=min(n_views_sample, V), replace=False))
+    t0 = time.perf_counter()
+    orc.filter(geom, g_np[views][None], None, views=views)
+    t_f = time.perf_counter() - t0
+    nvox = desc["vol_x"] * desc["vol_y"] * desc["vol_z"]
+    flat = rng.choice(nvox, size=min(n_vox_sample, nvox), replace=False)
+    gF = rng.standard_normal((V, desc["det_rows"], desc["det_cols"]))
+    t0 = time.perf_counter()
+    orc.backproject_points(geom, gF, flat)
+    t_b = time.perf_counter() - t0
+    ms = 1e3 * (t_f * V / len(views) + t_b * nvox / len(flat))
+    sample = (f"FP64 oracle filter on {len(views)} of {V} views and backprojection of "
+              f"{len(flat)} of {nvox} voxels over all views, scaled linearly to one volume")
+    return ms, sample, orc.num_threads(), t_f + t_b
+
+
+# --------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The oracle (this tier's reference) on the host cores, rank 0 only."""
+    from paper_2410_14900_gb300 import synth
+    if rank != 0:
+        return
+    w = synth.workload(args.workload)
+    # a small stand-in projection set is enough: the oracle's cost does not
+    # depend on the values
+    g = np.random.default_rng(0).standard_normal((w.n_views, w.det_rows, w.det_cols))
+    from oracle import oracle as orc
+    cores = orc.num_threads()
+    nv = max(1, min(cores, w.n_views))
+    nvox = 20000
+    for _ in range(args.warmup):
+        oracle_sample(w, g, 1, 1000)
+    times = []
+    sample = ""
+    for k in range(args.steps):
+        ms, sample, cores, _ = oracle_sample(w, g, nv, nvox, seed=k)
+        times.append(ms)
+    val = statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": val,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2410_14900_gb300 import _lib, api, synth
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    L = _lib.load()
+    w = synth.workload(args.workload)
+    desc = w.desc_dict()
+    geom = api.Geometry(desc, w.matrices(), w.orbit.vdl)
+    # every rank reconstructs its own seeded phantom
+    blobs = synth.random_ellipsoids(np.random.default_rng(w.seed + 1000 * rank),
+                                    w.n_objects, w.r_fov())
+    g = synth.project_phantom(blobs, w.orbit, w.det_rows, w.det_cols, w.pitch,
+                              device=dev, dtype=torch.float32)[None].contiguous()
+    B = 1
+    V, H, Wd = w.n_views, w.det_rows, w.det_cols
+    gF = torch.empty((B, V, H, Wd), device=dev,
+                     dtype={"f32": torch.float32, "bf16": torch.bfloat16,
+                            "f16": torch.float16}[args.storage])
+    scale = torch.empty((B, V), device=dev) if args.storage == "f16" else None
+    vol = torch.empty((B,) + geom.vol_shape, device=dev)
+    kahan = args.storage != "f32"
+
+    def step():
+        api.dc_filter(geom, g, None, args.storage, out=gF, scale=scale)
+        api.dc_backproject(geom, gF, scale, out=vol, kahan=kahan)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    api.dc_sync_status(geom)
+    barrier()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    L.dc_profile_enable(1)
+    L.dc_profile_collect(None, None, 0)
+    n0 = L.dc_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    n_launch = L.dc_launch_count() - n0
+    kid_n = 16
+    ms_k = (np.zeros(kid_n, dtype=np.float64))
+    cnt_k = (np.zeros(kid_n, dtype=np.uint64))
+    nk = L.dc_profile_collect(ms_k.ctypes.data, cnt_k.ctypes.data, kid_n)
+    L.dc_profile_enable(0)
+    clocks = sampler.stop()
+    barrier()
+    torch.cuda.synchronize()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    api.dc_sync_status(geom)
+
+    kernels = {}
+    for i in range(nk):
+        name = L.dc_profile_kernel_name(i).decode()
+        if cnt_k[i]:
+            kernels[name] = {"ms_total": float(ms_k[i]), "launches": int(cnt_k[i]),
+                             "ms_per_launch": float(ms_k[i] / cnt_k[i])}
+    units = work_units(desc, B)
+    peaks, peak_kind = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    roof = None
+    if dom in FLOPS_PER_UNIT:
+        per_launch_units = units[dom] * args.steps / kernels[dom]["launches"]
+        ach = per_launch_units * FLOPS_PER_UNIT[dom] / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops, "traffic": None,
+                "peak_source": f"FP32 issue rate: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x "
+                               f"2 x {sm_max:.0f} MHz (max clock of {peak_kind} peaks)",
+                "units_per_launch": per_launch_units,
+                "flops_per_unit": FLOPS_PER_UNIT[dom]}
+    filter_ms = sum(kernels.get(k, {}).get("ms_total", 0.0)
+                    for k in ("k_prep", "k_linesum", "k_bp2d", "k_to_f16")) / args.steps
+    bp_ms = kernels.get("k_bp3d", {}).get("ms_total", 0.0) / args.steps
+    hbm_bytes = (B * V * H * Wd * 4  # read g
+                 + 2 * B * V * H * Wd * gF.element_size()  # write + read g^F
+                 + vol.numel() * 4)  # write f
+    breakdown = {"filter_ms": filter_ms, "backproject_ms": bp_ms,
+                 "bp_gups": units["k_bp3d"] / (bp_ms * 1e-3) / 1e9 if bp_ms else None,
+                 "algorithmic_hbm_bytes": hbm_bytes,
+                 "hbm_frac_of_step": hbm_bytes / (ms_step * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6772.2),
+                 "kernels": kernels}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        g_host = g.cpu().pin_memory()
+        vol_host = torch.empty(vol.shape, dtype=torch.float32).pin_memory()
+        g_dev = torch.empty_like(g)
+
+        def e2e_step():
+            g_dev.copy_(g_host, non_blocking=True)
+            gF2, sc2 = api.dc_filter(geom, g_dev, None, args.storage, out=gF, scale=scale)
+            api.dc_backproject(geom, gF2, sc2, out=vol, kahan=kahan)
+            vol_host.copy_(vol, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e = a0.elapsed_time(a1) / args.steps
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": t_e2e / (B * world), "unit": UNIT,
+               "h2d_bytes_per_step": int(g.numel() * 4), "d2h_bytes_per_step": int(vol.numel() * 4)}
+
+    # the chosen low-precision form next to the plain FP32 path
+    forms = None
+    if not args.no_forms and args.storage == "f32":
+        forms = {}
+        for st in ("bf16", "f16"):
+            gF2 = torch.empty((B, V, H, Wd), device=dev,
+                              dtype=torch.bfloat16 if st == "bf16" else torch.float16)
+            sc2 = torch.empty((B, V), device=dev) if st == "f16" else None
+            for _ in range(2):
+                api.dc_filter(geom, g, None, st, out=gF2, scale=sc2)
+                api.dc_backproject(geom, gF2, sc2, out=vol, kahan=True)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(args.steps):
+                api.dc_filter(geom, g, None, st, out=gF2, scale=sc2)
+                api.dc_backproject(geom, gF2, sc2, out=vol, kahan=True)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            forms[f"{st}_storage_kahan_ms_per_volume"] = f0.elapsed_time(f1) / args.steps
+            del gF2
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g_np = g[0].double().cpu().numpy()
+        from oracle import oracle as orc
+        nv = max(1, min(orc.num_threads(), V))
+        ms, sample, cores, _ = oracle_sample(w, g_np, nv, 20000)
+        cpu = {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms_step / (B * world), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic: seeded 20-ellipsoid phantom, exact line integrals",
+                "config": {"workload": w.name, "orbit": w.orbit.kind, "views": V,
+                           "detector": [H, Wd], "pitch_mm": w.pitch,
+                           "planes": [w.n_mu, w.n_s], "volume": list(w.vol_shape),
+                           "voxel_mm": list(w.voxel), "storage": args.storage,
+                           "batch_per_gpu": B, "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (g 390 MB, f 537 MB), no flush"},
+                "roofline": roof, "breakdown": breakdown, "forms": forms,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(n_launch),
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    geom.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

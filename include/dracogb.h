@@ -1,0 +1,242 @@
+/*
+ * dracogb.h -- C ABI of the GB300 (sm_103a) Defrise-Clack shift-variant
+ * filtered backprojection for arbitrary cone-beam orbits (Ye et al., DRACO,
+ * arXiv 2410.14900, Sec. 2.2-2.3).
+ *
+ * The method (Eq. 12):
+ *     f = A3d^T w_d A2d^T D w_red w_sino D A2d w_cos g
+ * is split into two calls:
+ *     dc_filter       g   -> g^F = w_d A2d^T D w_red w_sino D A2d w_cos g
+ *                            (Eqs. 7, 8, 10, 11)
+ *     dc_backproject  g^F -> f = A3d^T g^F  (Eq. 5), optional ReLU
+ * plus their reverse-mode adjoints, so that the redundancy weights (the only
+ * trainable layer, Eq. 10) and the projections can be differentiated.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Units: mm and radians.  Row-major, contiguous arrays.
+ *  - Projections g, g^F: [B][V][H][W] (detector column index fastest).
+ *  - Volumes f: [B][Z][Y][X] (x fastest).  Voxel (ix,iy,iz) sits at
+ *    vol_center + ((ix-(X-1)/2) dx, (iy-(Y-1)/2) dy, (iz-(Z-1)/2) dz).
+ *  - Sinogram axes per view: mu_m = m pi / n_mu (m < n_mu),
+ *    s_k = (k - (n_s-1)/2) ds, measured from the principal point of the
+ *    detector (foot of the perpendicular from the source) along
+ *    (cos mu, sin mu) in the detector frame (l_x, l_y).
+ *  - Redundancy weights W: [V][n_mu][n_s]; entry k refers to the half-grid
+ *    abscissa s_{k+1/2} = s_k + ds/2 (the entry k = n_s-1 is unused).  The
+ *    library multiplies W by K = -(1/4pi^2)|v_i . theta| / sqrt(s^2+D^2),
+ *    where v_i = a'(lambda_i) dlambda_i; W = 1/2 is the exact circular-orbit
+ *    value (Eq. 14, M = 1/2).
+ *  - Projection matrices P: [V][3][4] FP64, host memory, mapping a
+ *    homogeneous world point to (col*w, row*w, w), w > 0 in front of the
+ *    source.  Pixels must be square with pitch `pitch`, without skew.
+ *  - Ownership: every array argument is caller-owned.  Pointers documented as
+ *    "device" must be CUDA device (or managed) memory on the current device;
+ *    "host" pointers are ordinary host memory.  The geometry handle owns only
+ *    its own device buffers (geometry tables and a work area).
+ *  - Execution: every compute call is asynchronous on the given stream
+ *    (a cudaStream_t passed as void*, NULL = the legacy default stream).  A
+ *    handle's work area is shared by its calls: do not use one handle on two
+ *    streams at the same time.  dc_setup_geometry is synchronous.
+ *  - Errors: every int-returning call returns DC_OK (0) or a DC_ERR_* code
+ *    and never throws; argument errors are detected before any work is
+ *    launched.  dc_last_error() gives a message for the calling thread's
+ *    last failure.
+ */
+#ifndef DRACOGB_H
+#define DRACOGB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DC_OK 0
+#define DC_ERR_ARG 1          /* invalid argument (NULL, size, layout)      */
+#define DC_ERR_CUDA 2         /* a CUDA runtime call or launch failed       */
+#define DC_ERR_OOM 3          /* device allocation failed                   */
+#define DC_ERR_TIMEOUT 4      /* a bounded device wait gave up              */
+#define DC_ERR_UNSUPPORTED 5  /* valid request this build does not handle  */
+
+/* storage types of the filtered projections g^F */
+#define DC_F32 0
+#define DC_BF16 1             /* round-to-nearest-even                      */
+#define DC_F16 2              /* with a per-view power-of-two scale         */
+
+/* dc_backproject flags */
+#define DC_ACCUM 1u           /* add into vol instead of overwriting        */
+#define DC_KAHAN 2u           /* compensated (Kahan) summation over views   */
+#define DC_RELU 4u            /* ReLU after the sum over views (Sec. 2.3)   */
+
+/* doubles per view returned by dc_get_view_geometry */
+#define DC_VIEW_GEO_N 24
+
+typedef struct {
+  int n_views;          /* V                                              */
+  int det_rows;         /* H                                              */
+  int det_cols;         /* W                                              */
+  int n_mu;             /* angles of the per-view 2D Radon transform      */
+  int n_s;              /* s-bins of the per-view 2D Radon transform      */
+  double pitch;         /* detector pixel pitch (mm), square pixels       */
+  double ds;            /* s-bin spacing (mm), ds >= pitch                */
+  int vol_x, vol_y, vol_z;
+  double voxel[3];      /* voxel size (dx, dy, dz) in mm                  */
+  double vol_center[3]; /* world position of the volume centre (mm)       */
+  int closed_orbit;     /* 1: the orbit is a closed curve (only used when
+                           the tangents are derived by finite differences) */
+} dc_geometry_desc;
+
+typedef struct dc_geometry dc_geometry;
+
+/*
+ * dc_setup_geometry -- per-view geometry of Fig. 1 (Sec. 2.3) from the
+ * projection matrices, computed in FP64 on the GPU: source a = -M^-1 p4,
+ * detector frame (l_x, l_y, l_z), source-detector distance D, principal
+ * point, and the orbit tangent v_i = a'(lambda_i) dlambda_i that enters the
+ * redundancy weight of Eq. 10.
+ *   desc : host, sizes and spacings (see the struct).
+ *   P    : host, [V][3][4] FP64.  Any nonzero scale; the sign is chosen so
+ *          that the volume centre has positive depth.
+ *   vdl  : host, [V][3] FP64 tangents a'(lambda)dlambda, or NULL to use
+ *          central differences of the sources (one-sided at the ends of an
+ *          open orbit, wrapped for closed_orbit = 1).
+ *   out  : receives the handle (destroy with dc_destroy_geometry).
+ * Returns DC_ERR_ARG for invalid sizes, a singular matrix, skew or
+ * non-square pixels; DC_ERR_OOM / DC_ERR_CUDA on device failures.
+ * Synchronous; uses the current CUDA device.
+ */
+int dc_setup_geometry(const dc_geometry_desc *desc, const double *P, const double *vdl,
+                      dc_geometry **out);
+
+/* Frees the handle and its device buffers (NULL is ignored). */
+void dc_destroy_geometry(dc_geometry *geom);
+
+/*
+ * dc_get_view_geometry -- copies the FP64 per-view geometry to host memory:
+ * out[V][DC_VIEW_GEO_N] = { a[3], l_x[3], l_y[3], l_z[3], D, c_u, c_v,
+ * v[3], |v|, 0, 0, 0 } (Fig. 1; c_u, c_v = principal point in pixels).
+ */
+int dc_get_view_geometry(const dc_geometry *geom, double *out);
+
+/*
+ * dc_filter -- the shift-variant filter of Eq. 11 applied to Grangeat's
+ * intermediate function of Eq. 7, for every view of every batch item:
+ *     g^F = w_d A2d^T D_b (W K) w_sino D_f A2d w_cos g
+ * A2d is Joseph's discrete 2D Radon transform over (mu, s); D_f/D_b are the
+ * forward/backward s-differences; A2d^T is the transpose of the Joseph
+ * weights times (pi/n_mu) ds/pitch^2 (the discrete integral over mu of
+ * Eq. 8); w_cos = D/sqrt(x^2+y^2+D^2), w_sino = (s^2+D^2)/D^2,
+ * w_d = x^2+y^2+D^2.
+ *   B       : batch size (>= 1); all items share the geometry and W.
+ *   g       : device, [B][V][H][W] FP32 projections.
+ *   W       : device, [V][n_mu][n_s] FP32 redundancy weights, or NULL for
+ *             the constant 1/2 (exact for a full circle, Eq. 14).
+ *   gF      : device, [B][V][H][W] output in `dtype` (DC_F32, DC_BF16,
+ *             DC_F16).
+ *   gF_scale: device, [B][V] FP32, required for DC_F16 (g^F = half * scale),
+ *             ignored otherwise.
+ * Requires ds >= pitch.
+ */
+int dc_filter(const dc_geometry *geom, int B, const float *g, const float *W, void *gF,
+              int dtype, float *gF_scale, void *stream);
+
+/*
+ * dc_filter_adjoint -- reverse mode of dc_filter (FP32 g^F): given
+ * grad_gF = dL/dg^F, writes dL/dg and dL/dW.  Grangeat's function S is
+ * recomputed from g view-chunk by view-chunk, so nothing from the forward
+ * pass needs to be kept.
+ *   grad_gF : device, [B][V][H][W] FP32.
+ *   g       : device, [B][V][H][W] FP32 (the forward input).
+ *   W       : device, [V][n_mu][n_s] FP32 or NULL (= 1/2).
+ *   grad_g  : device, [B][V][H][W] FP32 output, or NULL to skip.
+ *   grad_W  : device, [V][n_mu][n_s] FP32 output summed over the batch
+ *             (overwritten), or NULL to skip.
+ *   view_chunk: views processed together (0 = library default).
+ */
+int dc_filter_adjoint(const dc_geometry *geom, int B, const float *grad_gF, const float *g,
+                      const float *W, float *grad_g, float *grad_W, int view_chunk,
+                      void *stream);
+
+/*
+ * dc_backproject -- voxel-driven cone-beam backprojection of Eq. 5:
+ *     f(X) = sum_i bilinear(g^F_i, P_i X) / |X - a_i|^2
+ * Pixels outside the detector count as zero; voxels with depth <= 0 in a
+ * view get nothing from it.  Interpolation and accumulation are FP32 for
+ * every storage type.
+ *   gF      : device, [B][V][H][W] in `dtype`; gF_scale [B][V] for DC_F16.
+ *   vol     : device, [B][Z][Y][X] FP32, overwritten (or added to with
+ *             DC_ACCUM).
+ *   flags   : DC_ACCUM | DC_KAHAN | DC_RELU.
+ */
+int dc_backproject(const dc_geometry *geom, int B, const void *gF, int dtype,
+                   const float *gF_scale, float *vol, unsigned flags, void *stream);
+
+/*
+ * dc_backproject_adjoint -- transpose of dc_backproject (a voxel-driven
+ * cone-beam forward projector with the same bilinear weights and the same
+ * 1/|X - a|^2 factor):
+ *     grad_gF_i[pixel] = sum_X w_bilinear(pixel; P_i X) grad_vol(X) / |X-a_i|^2
+ *   grad_vol: device, [B][Z][Y][X] FP32.
+ *   relu_vol: device, [B][Z][Y][X] FP32 forward output when the forward used
+ *             DC_RELU (grad_vol is masked where relu_vol <= 0), else NULL.
+ *   grad_gF : device, [B][V][H][W] FP32, overwritten.
+ */
+int dc_backproject_adjoint(const dc_geometry *geom, int B, const float *grad_vol,
+                           const float *relu_vol, float *grad_gF, void *stream);
+
+/*
+ * Per-step entry points (the layers of Fig. 2), for testing and for callers
+ * that compose the network themselves.
+ *
+ * dc_grangeat -- S = w_sino D_f A2d w_cos g (Eq. 7) on the half grid
+ *   s_{k+1/2}: g device [B][V][H][W] FP32 -> S device [B][V][n_mu][n_s] FP32
+ *   (entry k = n_s-1 is zero).
+ * dc_radon2d -- Joseph A2d of arbitrary detector images, one per view of the
+ *   geometry (principal point of that view): img device [B][V][H][W] FP32 ->
+ *   R device [B][V][n_mu][n_s] FP32.
+ * dc_radon2d_adjoint -- the exact transpose of dc_radon2d (no mu-integral
+ *   scale): R device [B][V][n_mu][n_s] -> img device [B][V][H][W], overwritten.
+ */
+int dc_grangeat(const dc_geometry *geom, int B, const float *g, float *S, void *stream);
+int dc_radon2d(const dc_geometry *geom, int B, const float *img, float *R, void *stream);
+int dc_radon2d_adjoint(const dc_geometry *geom, int B, const float *R, float *img,
+                       void *stream);
+
+/*
+ * dc_sync_status -- waits for `stream`, then reports device-side failures of
+ * this handle's kernels since the last call: DC_ERR_TIMEOUT if a bounded
+ * wait inside a kernel gave up (the kernel then skipped its output).  Clears
+ * the flag.  Compute calls never block, so they cannot report this
+ * themselves.
+ */
+int dc_sync_status(const dc_geometry *geom, void *stream);
+
+/* Human-readable name of a status code (static storage). */
+const char *dc_status_string(int status);
+
+/* Message of the calling thread's most recent failure ("" if none). */
+const char *dc_last_error(void);
+
+/* Number of kernel launches this library has issued in this process. */
+unsigned long long dc_launch_count(void);
+
+/*
+ * Launch profiler.  While enabled, every kernel launch of this library is
+ * bracketed by CUDA events recorded on the launching stream.
+ * dc_profile_enable returns the previous state.  dc_profile_collect waits for
+ * the recorded events, writes per kernel id the summed device time (ms) and
+ * launch count since the previous collect into ms[n] / launches[n] (either
+ * may be NULL), resets the sums and returns the number of kernel ids.
+ * dc_profile_kernel_name maps an id to the kernel's name.
+ */
+int dc_profile_enable(int on);
+int dc_profile_collect(double *ms, unsigned long long *launches, int n);
+const char *dc_profile_kernel_name(int id);
+
+/* Library version string (static storage). */
+const char *dc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DRACOGB_H */

@@ -1,0 +1,243 @@
+"""Python binding of the C ABI in include/dracogb.h (argument marshalling only).
+
+Every function has the name of its C entry point and forwards torch CUDA
+tensors as raw device pointers on the current torch stream; all arithmetic
+runs in the CUDA library.  Layouts (Ye et al., DRACO, Eq. 12):
+
+    g, g^F : [B, V, H, W]          volume : [B, Z, Y, X]
+    W      : [V, n_mu, n_s]        S, R   : [B, V, n_mu, n_s]
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import DC_ACCUM, DC_BF16, DC_F16, DC_F32, DC_KAHAN, DC_RELU, check
+
+_DTYPES = {"f32": (DC_F32, torch.float32), "bf16": (DC_BF16, torch.bfloat16),
+           "f16": (DC_F16, torch.float16)}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _need(t: torch.Tensor, name: str, dtype, shape):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+class Geometry:
+    """Owner of a dc_geometry handle (dc_setup_geometry / dc_destroy_geometry)."""
+
+    def __init__(self, desc: dict, P, vdl=None):
+        L = _lib.load()
+        d = _lib.dc_geometry_desc()
+        d.n_views, d.det_rows, d.det_cols = desc["n_views"], desc["det_rows"], desc["det_cols"]
+        d.n_mu, d.n_s = desc["n_mu"], desc["n_s"]
+        d.pitch, d.ds = desc["pitch"], desc["ds"]
+        d.vol_x, d.vol_y, d.vol_z = desc["vol_x"], desc["vol_y"], desc["vol_z"]
+        for t in range(3):
+            d.voxel[t] = desc["voxel"][t]
+            d.vol_center[t] = desc.get("vol_center", (0.0, 0.0, 0.0))[t]
+        d.closed_orbit = int(desc.get("closed_orbit", 1))
+        self.desc = dict(desc)
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        if P.size != 12 * d.n_views:
+            raise ValueError("P must hold n_views 3x4 matrices")
+        v = None if vdl is None else np.ascontiguousarray(vdl, dtype=np.float64)
+        if v is not None and v.size != 3 * d.n_views:
+            raise ValueError("vdl must hold n_views 3-vectors")
+        h = ctypes.c_void_p()
+        rc = L.dc_setup_geometry(ctypes.byref(d), P.ctypes.data_as(ctypes.c_void_p),
+                                 None if v is None else v.ctypes.data_as(ctypes.c_void_p),
+                                 ctypes.byref(h))
+        check(rc, "dc_setup_geometry")
+        self._h = h
+        self._lib = L
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("geometry already destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self._lib.dc_destroy_geometry(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # sizes
+    @property
+    def V(self):
+        return self.desc["n_views"]
+
+    @property
+    def H(self):
+        return self.desc["det_rows"]
+
+    @property
+    def W(self):
+        return self.desc["det_cols"]
+
+    @property
+    def vol_shape(self):
+        return (self.desc["vol_z"], self.desc["vol_y"], self.desc["vol_x"])
+
+    @property
+    def sino_shape(self):
+        return (self.desc["n_mu"], self.desc["n_s"])
+
+
+def dc_setup_geometry(desc: dict, P, vdl=None) -> Geometry:
+    return Geometry(desc, P, vdl)
+
+
+def dc_destroy_geometry(geom: Geometry):
+    geom.close()
+
+
+def dc_get_view_geometry(geom: Geometry) -> np.ndarray:
+    out = np.zeros((geom.V, _lib.DC_VIEW_GEO_N))
+    check(_lib.load().dc_get_view_geometry(geom.handle, out.ctypes.data_as(ctypes.c_void_p)),
+          "dc_get_view_geometry")
+    return out
+
+
+def dc_filter(geom: Geometry, g: torch.Tensor, W: Optional[torch.Tensor] = None,
+              dtype: str = "f32", out: Optional[torch.Tensor] = None,
+              scale: Optional[torch.Tensor] = None):
+    """g^F = w_d A2d^T D_b (W K) w_sino D_f A2d w_cos g (Eq. 11).  Returns (g^F, scale)."""
+    B = g.shape[0]
+    _need(g, "g", torch.float32, (B, geom.V, geom.H, geom.W))
+    if W is not None:
+        _need(W, "W", torch.float32, (geom.V,) + geom.sino_shape)
+    code, tdt = _DTYPES[dtype]
+    if out is None:
+        out = torch.empty((B, geom.V, geom.H, geom.W), device=g.device, dtype=tdt)
+    _need(out, "gF", tdt, (B, geom.V, geom.H, geom.W))
+    if code == DC_F16 and scale is None:
+        scale = torch.empty((B, geom.V), device=g.device, dtype=torch.float32)
+    rc = _lib.load().dc_filter(geom.handle, B, _ptr(g), _ptr(W), _ptr(out), code,
+                               _ptr(scale if code == DC_F16 else None), _stream())
+    check(rc, "dc_filter")
+    return out, (scale if code == DC_F16 else None)
+
+
+def dc_filter_adjoint(geom: Geometry, grad_gF: torch.Tensor, g: torch.Tensor,
+                      W: Optional[torch.Tensor] = None, want_grad_g: bool = True,
+                      want_grad_W: bool = True, view_chunk: int = 0):
+    """Reverse mode of dc_filter: returns (dL/dg or None, dL/dW or None)."""
+    B = g.shape[0]
+    shp = (B, geom.V, geom.H, geom.W)
+    _need(g, "g", torch.float32, shp)
+    _need(grad_gF, "grad_gF", torch.float32, shp)
+    if W is not None:
+        _need(W, "W", torch.float32, (geom.V,) + geom.sino_shape)
+    gg = torch.empty(shp, device=g.device, dtype=torch.float32) if want_grad_g else None
+    gW = (torch.empty((geom.V,) + geom.sino_shape, device=g.device, dtype=torch.float32)
+          if want_grad_W else None)
+    rc = _lib.load().dc_filter_adjoint(geom.handle, B, _ptr(grad_gF), _ptr(g), _ptr(W),
+                                       _ptr(gg), _ptr(gW), int(view_chunk), _stream())
+    check(rc, "dc_filter_adjoint")
+    return gg, gW
+
+
+def dc_backproject(geom: Geometry, gF: torch.Tensor, scale: Optional[torch.Tensor] = None,
+                   out: Optional[torch.Tensor] = None, accum: bool = False,
+                   kahan: bool = False, relu: bool = False) -> torch.Tensor:
+    """f = A3d^T g^F (Eq. 5), optional ReLU; g^F in f32, bf16 or f16 (+scale)."""
+    B = gF.shape[0]
+    code = {torch.float32: DC_F32, torch.bfloat16: DC_BF16, torch.float16: DC_F16}[gF.dtype]
+    _need(gF, "gF", gF.dtype, (B, geom.V, geom.H, geom.W))
+    if code == DC_F16:
+        if scale is None:
+            raise ValueError("f16 g^F needs its scale")
+        _need(scale, "scale", torch.float32, (B, geom.V))
+    if out is None:
+        if accum:
+            raise ValueError("accum needs an output volume")
+        out = torch.empty((B,) + geom.vol_shape, device=gF.device, dtype=torch.float32)
+    _need(out, "vol", torch.float32, (B,) + geom.vol_shape)
+    flags = (DC_ACCUM if accum else 0) | (DC_KAHAN if kahan else 0) | (DC_RELU if relu else 0)
+    rc = _lib.load().dc_backproject(geom.handle, B, _ptr(gF), code,
+                                    _ptr(scale if code == DC_F16 else None), _ptr(out),
+                                    flags, _stream())
+    check(rc, "dc_backproject")
+    return out
+
+
+def dc_backproject_adjoint(geom: Geometry, grad_vol: torch.Tensor,
+                           relu_vol: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """(A3d^T)^T grad_vol -> [B, V, H, W]; masked where relu_vol <= 0 if given."""
+    B = grad_vol.shape[0]
+    _need(grad_vol, "grad_vol", torch.float32, (B,) + geom.vol_shape)
+    if relu_vol is not None:
+        _need(relu_vol, "relu_vol", torch.float32, (B,) + geom.vol_shape)
+    out = torch.empty((B, geom.V, geom.H, geom.W), device=grad_vol.device, dtype=torch.float32)
+    rc = _lib.load().dc_backproject_adjoint(geom.handle, B, _ptr(grad_vol), _ptr(relu_vol),
+                                            _ptr(out), _stream())
+    check(rc, "dc_backproject_adjoint")
+    return out
+
+
+def dc_grangeat(geom: Geometry, g: torch.Tensor) -> torch.Tensor:
+    """S = w_sino D_f A2d w_cos g on the half grid (Eq. 7)."""
+    B = g.shape[0]
+    _need(g, "g", torch.float32, (B, geom.V, geom.H, geom.W))
+    S = torch.empty((B, geom.V) + geom.sino_shape, device=g.device, dtype=torch.float32)
+    check(_lib.load().dc_grangeat(geom.handle, B, _ptr(g), _ptr(S), _stream()), "dc_grangeat")
+    return S
+
+
+def dc_radon2d(geom: Geometry, img: torch.Tensor) -> torch.Tensor:
+    """Joseph A2d of per-view detector images."""
+    B = img.shape[0]
+    _need(img, "img", torch.float32, (B, geom.V, geom.H, geom.W))
+    R = torch.empty((B, geom.V) + geom.sino_shape, device=img.device, dtype=torch.float32)
+    check(_lib.load().dc_radon2d(geom.handle, B, _ptr(img), _ptr(R), _stream()), "dc_radon2d")
+    return R
+
+
+def dc_radon2d_adjoint(geom: Geometry, R: torch.Tensor) -> torch.Tensor:
+    """Exact transpose of dc_radon2d."""
+    B = R.shape[0]
+    _need(R, "R", torch.float32, (B, geom.V) + geom.sino_shape)
+    img = torch.empty((B, geom.V, geom.H, geom.W), device=R.device, dtype=torch.float32)
+    check(_lib.load().dc_radon2d_adjoint(geom.handle, B, _ptr(R), _ptr(img), _stream()),
+          "dc_radon2d_adjoint")
+    return img
+
+
+def dc_sync_status(geom: Geometry):
+    """Wait for the current stream; raise if a device-side wait timed out."""
+    check(_lib.load().dc_sync_status(geom.handle, _stream()), "dc_sync_status")
+
+
+def reconstruct(geom: Geometry, g: torch.Tensor, W: Optional[torch.Tensor] = None,
+                dtype: str = "f32", kahan: bool = False, relu: bool = False) -> torch.Tensor:
+    """Eq. 12: f = A3d^T w_d A2d^T D w_red w_sino D A2d w_cos g."""
+    gF, sc = dc_filter(geom, g, W, dtype)
+    return dc_backproject(geom, gF, sc, kahan=kahan, relu=relu)

@@ -1,0 +1,996 @@
+// dc_filter.cu -- the filtering part of the Defrise-Clack network
+// (Ye et al., DRACO, Sec. 2.3, Eqs. 7, 8, 10, 11):
+//
+//   S   = w_sino D_f A2d w_cos g                (Grangeat's function, Eq. 7)
+//   g^F = w_d A2d^T D_b (W K) S                 (shift-variant filter, Eq. 11)
+//
+// and its reverse mode.  Views are processed in chunks of images (view x
+// batch item) so that the work area stays in L2:
+//
+//   k_prep      weight (w_cos or w_d) and write the image and its transpose
+//   k_linesum   Joseph line sums of every (mu, s) line of an image, streamed
+//               row band by row band through shared memory with bulk copies;
+//               neighbouring lines of a warp take the s-difference by shuffle
+//               so that D_f never subtracts two large sums; the epilogue
+//               applies w_sino, K, W and D_b (or the adjoint chain)
+//   k_bp2d      pixel-driven A2d^T: each pixel gathers the two sinogram taps
+//               of every angle (the exact transpose of the Joseph weights),
+//               angles streamed through shared memory with bulk copies; the
+//               epilogue applies w_d (forward) or w_cos (adjoint)
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "dc_async.cuh"
+#include "dc_common.cuh"
+
+namespace {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr int PADL = 4;  // zero floats left of every shared-memory row (16 B)
+constexpr int PADR = 4;  // zero floats right of every shared-memory row
+
+// ------------------------------------------------------------------ prep
+enum { WT_NONE = 0, WT_COS = 1, WT_D = 2 };
+
+struct PrepArgs {
+  const float *src;  // [B][V][H][W]
+  float *img;        // [n][H][Wp]
+  float *imgT;       // [n][W][Hp]
+  const dc::FView *fv;
+  int H, W, Wp, Hp, V, B, v0, n_img;  // B = batch items in this chunk
+  int b0, Bt;                         // first item of the chunk, total batch
+  float pitch;
+  int weight;
+};
+
+// 32x32 tiles, transposed through shared memory; pads are written as zeros.
+__global__ void __launch_bounds__(256) k_prep(PrepArgs a) {
+  __shared__ float tile[32][33];
+  int n = blockIdx.z;
+  int v = a.v0 + n / a.B, b = a.b0 + n % a.B;
+  const dc::FView f = a.fv[v];
+  const float *src = a.src + ((size_t)b * a.V + v) * a.H * a.W;
+  int j0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  int tx = threadIdx.x, ty = threadIdx.y;
+  for (int q = ty; q < 32; q += 8) {
+    int r = r0 + q, j = j0 + tx;
+    float val = 0.0f;
+    if (r < a.H && j < a.W) {
+      val = src[(size_t)r * a.W + j];
+      if (a.weight != WT_NONE) {
+        float x = (j - f.cu) * a.pitch, y = (r - f.cv) * a.pitch;
+        float l2 = fmaf(x, x, fmaf(y, y, f.D * f.D));
+        val *= (a.weight == WT_COS) ? f.D * rsqrtf(l2) : l2;
+      }
+    }
+    tile[q][tx] = val;
+    if (r < a.H && j < a.Wp) a.img[((size_t)n * a.H + r) * a.Wp + j] = val;
+  }
+  __syncthreads();
+  for (int q = ty; q < 32; q += 8) {
+    int j = j0 + q, r = r0 + tx;
+    if (j < a.W && r < a.Hp) a.imgT[((size_t)n * a.W + j) * a.Hp + r] = tile[tx][q];
+  }
+}
+
+// ------------------------------------------------------------- line sums
+enum { M_RAW = 0, M_GRANGEAT = 1, M_FILTER = 2, M_DIFFSTORE = 3, M_ADJ = 4 };
+
+constexpr int LS_THREADS = 256;
+constexpr int LS_WARPS = LS_THREADS / 32;
+constexpr int LS_RB = 16;    // detector rows per band
+constexpr int LS_TPW = 16;   // max (angle, 31-line chunk) tasks per warp
+
+struct LineArgs {
+  const float *img;   // [n][H][Wp]
+  const float *imgT;  // [n][W][Hp]
+  int H, W, Wp, Hp;
+  int n_mu, n_s, NSp;
+  int V, B, v0, n_img;  // B = batch items in this chunk
+  int b0;               // first batch item of the chunk
+  float pitch, ds, cT;  // cT = (pi/n_mu) ds / pitch^2
+  const dc::MuRec *mu;
+  const int *mu_order;
+  const dc::MuGroup *groups;
+  const dc::FView *fv;
+  const float *Wred;   // [V][n_mu][n_s] or NULL (= 1/2)
+  float *out;          // RAW/GRANGEAT: user [B][V][n_mu][n_s]; else scratch [n][n_mu][NSp]
+  float *sinoA;        // DIFFSTORE out / ADJ in-out (scratch)
+  float *sinoB;        // ADJ out (scratch)
+  unsigned *err;
+  int mg;              // max angles per group
+};
+
+// per-angle constants of one CTA, computed in FP64 and stored as float pairs
+struct LineMu {
+  float b0i, b0f;    // c_col + c_row sn/cs  = b0i (integer) + b0f
+  float a_hi, a_lo;  // (ds/p)/cs  (hi has 12 fractional bits)
+  float d_hi, d_lo;  // -sn/cs     (slope per row)
+  float dxi;         // -sn/cs as a float
+  float jscale;      // p / |cs|
+};
+
+__device__ __forceinline__ float split_hi(double v) {
+  return (float)(rint(v * 4096.0) / 4096.0);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(LS_THREADS) k_linesum(LineArgs a) {
+  constexpr bool DIFF = (MODE != M_RAW);
+  constexpr int STRIDE_L = DIFF ? 31 : 32;  // lines per task (diff: one overlap)
+  extern __shared__ __align__(16) float smem[];
+  __shared__ uint64_t bars[2];
+  __shared__ LineMu lmu[8];
+  __shared__ int sh_err;
+
+  const int n = blockIdx.y;
+  const dc::MuGroup G = a.groups[blockIdx.x];
+  const int v = a.v0 + n / a.B, b = a.b0 + n % a.B;
+  const dc::FView fv = a.fv[v];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // streamed image: branch 0 steps over detector rows of img, branch 1 over
+  // detector columns, i.e. the rows of the transposed image
+  const int rows = G.branch ? a.W : a.H;   // steps along a line
+  const int len = G.branch ? a.H : a.W;    // samples across a line
+  const int lenp = G.branch ? a.Hp : a.Wp;
+  const int rstride = lenp + PADL + PADR;
+  const float *src = G.branch ? a.imgT + (size_t)n * a.W * a.Hp : a.img + (size_t)n * a.H * a.Wp;
+  float *stage0 = smem;
+  float *stage1 = smem + LS_RB * rstride;
+  float *ep = smem + 2 * LS_RB * rstride;  // [mg][NSp] epilogue buffer
+
+  if (threadIdx.x == 0) {
+    dc::mbar_init(&bars[0], 1);
+    dc::mbar_init(&bars[1], 1);
+    dc::fence_barrier_init();
+    sh_err = 0;
+  }
+  if (threadIdx.x < G.count) {
+    int m = a.mu_order[G.first + threadIdx.x];
+    double ang = (double)m * 3.14159265358979323846 / a.n_mu;
+    double cm = cos(ang), sm = sin(ang);
+    double cs = G.branch ? sm : cm, sn = G.branch ? cm : sm;
+    double ccol = G.branch ? fv.cv : fv.cu, crow = G.branch ? fv.cu : fv.cv;
+    double b0 = ccol + crow * sn / cs;
+    double A = ((double)a.ds / a.pitch) / cs;
+    double dx = -sn / cs;
+    LineMu L;
+    L.b0i = (float)floor(b0);
+    L.b0f = (float)(b0 - floor(b0));
+    L.a_hi = split_hi(A);
+    L.a_lo = (float)(A - (double)L.a_hi);
+    L.d_hi = split_hi(dx);
+    L.d_lo = (float)(dx - (double)L.d_hi);
+    L.dxi = (float)dx;
+    L.jscale = (float)((double)a.pitch / fabs(cs));
+    lmu[threadIdx.x] = L;
+  }
+  // zero the row pads of both stages (never written by the bulk copies)
+  for (int i = threadIdx.x; i < 2 * LS_RB; i += LS_THREADS) {
+    float *row = smem + (size_t)i * rstride;
+    for (int t = 0; t < PADL; ++t) row[t] = 0.0f;
+    for (int t = PADL + lenp; t < rstride; ++t) row[t] = 0.0f;
+  }
+  __syncthreads();
+
+  const int nbands = (rows + LS_RB - 1) / LS_RB;
+  auto issue = [&](int band) {
+    int r0 = band * LS_RB;
+    int nr = min(LS_RB, rows - r0);
+    uint64_t *bar = &bars[band & 1];
+    float *st = (band & 1) ? stage1 : stage0;
+    dc::fence_proxy_async();
+    dc::mbar_arrive_expect_tx(bar, (unsigned)(nr * lenp * 4));
+    for (int q = 0; q < nr; ++q)
+      dc::bulk_g2s(st + (size_t)q * rstride + PADL, src + (size_t)(r0 + q) * lenp,
+                   (unsigned)(lenp * 4), bar);
+  };
+  if (threadIdx.x == 0) {
+    issue(0);
+    if (nbands > 1) issue(1);
+  }
+
+  // tasks: (angle of the group, chunk of STRIDE_L lines); lane = line in chunk
+  const int nch = (a.n_s - (DIFF ? 1 : 0) + STRIDE_L - 1) / STRIDE_L;
+  const int ntask = G.count * nch;
+  int X0i[LS_TPW];
+  float x0f[LS_TPW], acc[LS_TPW];
+#pragma unroll
+  for (int tt = 0; tt < LS_TPW; ++tt) {
+    acc[tt] = 0.0f;
+    X0i[tt] = 0;
+    x0f[tt] = 0.0f;
+    int t = warp + LS_WARPS * tt;
+    if (t < ntask) {
+      const LineMu &L = lmu[t / nch];
+      int k = (t % nch) * STRIDE_L + lane;
+      k = min(k, a.n_s - 1);
+      float kk = (float)k - 0.5f * (float)(a.n_s - 1);  // half-integer or integer
+      // x0 = b0 + kk * A, split into integer and fraction without FP64
+      float t1 = kk * L.a_hi;  // exact
+      float t1i = floorf(t1);
+      float fr = L.b0f + (t1 - t1i) + kk * L.a_lo;
+      float fri = floorf(fr);
+      X0i[tt] = (int)L.b0i + (int)t1i + (int)fri;
+      x0f[tt] = fr - fri;
+    }
+  }
+
+  bool ok = true;
+  for (int band = 0; band < nbands; ++band) {
+    if (!dc::mbar_wait_bounded(&bars[band & 1], (band >> 1) & 1, a.err)) ok = false;
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+    const float *st = (band & 1) ? stage1 : stage0;
+    const int r0 = band * LS_RB;
+    const int nr = min(LS_RB, rows - r0);
+#pragma unroll
+    for (int tt = 0; tt < LS_TPW; ++tt) {
+      int t = warp + LS_WARPS * tt;
+      if (t >= ntask) break;
+      const LineMu &L = lmu[t / nch];
+      // anchor of this band: xi(r0) = J + fb, exactly split
+      float r0f = (float)r0;
+      float th = r0f * L.d_hi;  // exact
+      float thi = floorf(th);
+      float fr = x0f[tt] + (th - thi) + r0f * L.d_lo;
+      float fri = floorf(fr);
+      int J = X0i[tt] + (int)thi + (int)fri;
+      float fb = fr - fri;
+      const float dxi = L.dxi;
+      float lo = (float)(-1 - J), hi = (float)(len - J);
+      float xa = fb, xb = fmaf((float)(nr - 1), dxi, fb);
+      float xmin = fminf(xa, xb), xmax = fmaxf(xa, xb);
+      bool outside = (xmax <= lo) || (xmin >= hi);
+      if (__all_sync(0xffffffffu, outside)) continue;  // the band misses these lines
+      bool inside = (xmin >= lo + 1.0f) && (xmax <= hi - 1.0f);
+      const float *base = st + PADL + J;
+      float sum = 0.0f;
+      if (__all_sync(0xffffffffu, inside)) {
+#pragma unroll 4
+        for (int q = 0; q < nr; ++q) {
+          float x = fmaf((float)q, dxi, fb), f;
+          int j = dc::floor_frac(x, f);
+          const float *p = base + q * rstride + j;
+          float g0 = p[0], g1 = p[1];
+          sum += fmaf(f, g1 - g0, g0);
+        }
+      } else {
+#pragma unroll 4
+        for (int q = 0; q < nr; ++q) {
+          float x = fminf(fmaxf(fmaf((float)q, dxi, fb), lo), hi), f;
+          int j = dc::floor_frac(x, f);
+          const float *p = base + q * rstride + j;
+          float g0 = p[0], g1 = p[1];
+          sum += fmaf(f, g1 - g0, g0);
+        }
+      }
+      if (DIFF) {
+        float nb = __shfl_down_sync(0xffffffffu, sum, 1);
+        acc[tt] += nb - sum;
+      } else {
+        acc[tt] += sum;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && band + 2 < nbands) issue(band + 2);
+  }
+  if (!ok) {
+    // drain: give the copies still in flight a bounded chance to land
+    for (int s = 0; s < 2; ++s) dc::mbar_wait_bounded(&bars[s], 0, nullptr);
+    return;
+  }
+
+  // line sums (RAW) or differences R_{k+1}-R_k (DIFF) into the epilogue buffer
+#pragma unroll
+  for (int tt = 0; tt < LS_TPW; ++tt) {
+    int t = warp + LS_WARPS * tt;
+    if (t >= ntask) break;
+    int ml = t / nch;
+    int k = (t % nch) * STRIDE_L + lane;
+    bool valid = DIFF ? (lane < 31 && k <= a.n_s - 2) : (k <= a.n_s - 1);
+    if (valid) ep[ml * a.NSp + k] = acc[tt] * lmu[ml].jscale;
+  }
+  __syncthreads();
+
+  const float D = fv.D, D2 = D * D;
+  const float inv4pi2 = 1.0f / (4.0f * kPi * kPi);
+  const int total = G.count * a.NSp;
+  auto s_half = [&](int k) { return ((float)k - 0.5f * (float)(a.n_s - 1) + 0.5f) * a.ds; };
+  auto Kw = [&](int m, float sh) {  // -(1/4pi^2)|v.theta|/sqrt(s^2+D^2)
+    const dc::MuRec r = a.mu[m];
+    float vt = fmaf(sh, fv.az, D * fmaf(r.c, fv.ax, r.s * fv.ay));
+    return -fabsf(vt) * inv4pi2 / fmaf(sh, sh, D2);
+  };
+
+  if (MODE == M_RAW || MODE == M_GRANGEAT) {
+    for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
+      int ml = idx / a.NSp, k = idx % a.NSp;
+      if (k >= a.n_s) continue;
+      int m = a.mu_order[G.first + ml];
+      float val;
+      if (MODE == M_RAW) {
+        val = ep[idx];
+      } else {
+        float sh = s_half(k);
+        val = (k <= a.n_s - 2) ? ep[idx] * (fmaf(sh, sh, D2) / D2) / a.ds : 0.0f;
+      }
+      a.out[(((size_t)b * a.V + v) * a.n_mu + m) * a.n_s + k] = val;
+    }
+    return;
+  }
+  if (MODE == M_DIFFSTORE) {
+    for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
+      int ml = idx / a.NSp, k = idx % a.NSp;
+      int m = a.mu_order[G.first + ml];
+      a.sinoA[((size_t)n * a.n_mu + m) * a.NSp + k] = (k <= a.n_s - 2) ? ep[idx] : 0.0f;
+    }
+    return;
+  }
+  if (MODE == M_FILTER) {
+    // Q = W K w_sino (R_{k+1}-R_k)/ds on s_{k+1/2}
+    for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
+      int ml = idx / a.NSp, k = idx % a.NSp;
+      int m = a.mu_order[G.first + ml];
+      float q = 0.0f;
+      if (k <= a.n_s - 2) {
+        float sh = s_half(k);
+        float w = a.Wred ? a.Wred[((size_t)v * a.n_mu + m) * a.n_s + k] : 0.5f;
+        q = w * Kw(m, sh) * (fmaf(sh, sh, D2) / D2) * ep[idx] / a.ds;
+      }
+      ep[idx] = q;
+    }
+    __syncthreads();
+    // P = D_b Q, times the A2d^T scale (pi/n_mu)(ds/p^2) and the Joseph scale
+    for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
+      int ml = idx / a.NSp, k = idx % a.NSp;
+      int m = a.mu_order[G.first + ml];
+      float val = 0.0f;
+      if (k < a.n_s) {
+        float qm = (k > 0) ? ep[idx - 1] : 0.0f;
+        val = (ep[idx] - qm) / a.ds * a.cT * lmu[ml].jscale;
+      }
+      a.out[((size_t)n * a.n_mu + m) * a.NSp + k] = val;
+    }
+    return;
+  }
+  if (MODE == M_ADJ) {
+    // sinoA holds jscale*(R_G[k+1]-R_G[k]) of w_d*dL/dg^F; this launch's
+    // line differences are those of w_cos*g (Grangeat's S, recomputed).
+    for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
+      int ml = idx / a.NSp, k = idx % a.NSp;
+      int m = a.mu_order[G.first + ml];
+      size_t o = ((size_t)n * a.n_mu + m) * a.NSp + k;
+      float y = 0.0f, tW = 0.0f;
+      if (k <= a.n_s - 2) {
+        float sh = s_half(k);
+        float wsino = fmaf(sh, sh, D2) / D2;
+        float S = wsino * ep[idx] / a.ds;
+        float Qg = -a.cT * a.sinoA[o] / a.ds;  // D_b^T of dL/dP
+        float Kv = Kw(m, sh);
+        float w = a.Wred ? a.Wred[((size_t)v * a.n_mu + m) * a.n_s + k] : 0.5f;
+        tW = Kv * S * Qg;                       // dL/dW contribution
+        y = wsino * w * Kv * Qg;                // dL/dS times w_sino
+      }
+      a.sinoA[o] = tW;
+      ep[idx] = y;
+    }
+    __syncthreads();
+    // dL/dR = D_f^T y; times the Joseph scale for the transpose gather
+    for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
+      int ml = idx / a.NSp, k = idx % a.NSp;
+      int m = a.mu_order[G.first + ml];
+      float val = 0.0f;
+      if (k < a.n_s) {
+        float ym = (k > 0) ? ep[idx - 1] : 0.0f;
+        float y0 = (k <= a.n_s - 2) ? ep[idx] : 0.0f;
+        val = (ym - y0) / a.ds * lmu[ml].jscale;
+      }
+      a.sinoB[((size_t)n * a.n_mu + m) * a.NSp + k] = val;
+    }
+  }
+}
+
+// ----------------------------------------------------- 2-D backprojection
+constexpr int BP2_THREADS = 256;
+constexpr int BP2_NQ = 2;   // x positions per thread (lane, lane+32)
+constexpr int BP2_RY = 4;   // rows per warp
+constexpr int BP2_TX = 32 * BP2_NQ;
+constexpr int BP2_TY = 8 * BP2_RY;
+constexpr int BP2_MC = 16;  // angles per stage
+
+enum { OUT_F32 = 0, OUT_BF16 = 1, OUT_F32_ABSMAX = 2 };
+
+struct BP2Args {
+  const float *sino;  // [n][n_mu][NSp], pre-scaled by the Joseph and mu scales
+  int H, W, n_mu, n_s, NSp;
+  int V, B, v0, n_img;  // B = batch items in this chunk
+  int b0;
+  float pitch, ds;
+  const dc::FView *fv;
+  int weight;          // WT_NONE / WT_COS / WT_D
+  int out_kind;        // OUT_*
+  void *out;           // user [B][V][H][W] (f32 or bf16) or scratch [n][H][Wp] f32
+  int Wp;
+  unsigned *absmax;    // [n] (OUT_F32_ABSMAX)
+  unsigned *err;
+};
+
+struct BPMu {
+  float F00, I00, Bc, Bs, winv, pad0, pad1, pad2;
+};
+
+__global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ uint64_t bars[2];
+  __shared__ BPMu bmu[2][BP2_MC];
+  const int n = blockIdx.z;
+  const int v = a.v0 + n / a.B, b = a.b0 + n % a.B;
+  const dc::FView fv = a.fv[v];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j0 = blockIdx.x * BP2_TX, r0 = blockIdx.y * BP2_TY;
+  const int rstride = a.NSp + PADL + PADR;
+  const int stage_sz = BP2_MC * rstride;
+  const float *src = a.sino + (size_t)n * a.n_mu * a.NSp;
+  const int nchunk = (a.n_mu + BP2_MC - 1) / BP2_MC;
+
+  if (threadIdx.x == 0) {
+    dc::mbar_init(&bars[0], 1);
+    dc::mbar_init(&bars[1], 1);
+    dc::fence_barrier_init();
+  }
+  for (int i = threadIdx.x; i < 2 * BP2_MC; i += BP2_THREADS) {
+    float *row = smem + (size_t)i * rstride;
+    for (int t = 0; t < PADL; ++t) row[t] = 0.0f;
+    for (int t = PADL + a.NSp; t < rstride; ++t) row[t] = 0.0f;
+  }
+  __syncthreads();
+  auto issue = [&](int c) {
+    int m0 = c * BP2_MC, nm = min(BP2_MC, a.n_mu - m0);
+    uint64_t *bar = &bars[c & 1];
+    dc::fence_proxy_async();
+    dc::mbar_arrive_expect_tx(bar, (unsigned)(nm * a.NSp * 4));
+    for (int q = 0; q < nm; ++q)
+      dc::bulk_g2s(smem + (c & 1) * stage_sz + (size_t)q * rstride + PADL, src + (size_t)(m0 + q) * a.NSp,
+                   (unsigned)(a.NSp * 4), bar);
+  };
+  // per-angle constants (FP64 once per CTA and angle): xi(j, r) = position of
+  // pixel (j, r) on the s grid, in s-bin units; xi(j0+jl, r0+rl) =
+  // I00 + F00 + jl*Bc + rl*Bs
+  auto angle_consts = [&](int c) {
+    int mi = threadIdx.x;
+    int m = c * BP2_MC + mi;
+    if (mi < BP2_MC && m < a.n_mu) {
+      double ang = (double)m * 3.14159265358979323846 / a.n_mu;
+      double cm = cos(ang), sm = sin(ang);
+      double k = (double)a.pitch / a.ds;
+      double xi = 0.5 * (a.n_s - 1) + ((j0 - (double)fv.cu) * cm + (r0 - (double)fv.cv) * sm) * k;
+      double fl = floor(xi);
+      // the Joseph branch decides the hat half-width p * max(|cos|, |sin|)
+      bool rowsb = (4 * m <= a.n_mu) || (4 * m >= 3 * a.n_mu);
+      double mx = rowsb ? fabs(cm) : fabs(sm);
+      BPMu M;
+      M.I00 = (float)fl;
+      M.F00 = (float)(xi - fl);
+      M.Bc = (float)(cm * k);
+      M.Bs = (float)(sm * k);
+      M.winv = (float)((double)a.ds / ((double)a.pitch * mx));
+      M.pad0 = M.pad1 = M.pad2 = 0.0f;
+      bmu[c & 1][mi] = M;
+    }
+  };
+  if (threadIdx.x == 0) {
+    issue(0);
+    if (nchunk > 1) issue(1);
+  }
+  angle_consts(0);
+
+  float acc[BP2_RY][BP2_NQ];
+#pragma unroll
+  for (int ry = 0; ry < BP2_RY; ++ry)
+#pragma unroll
+    for (int q = 0; q < BP2_NQ; ++q) acc[ry][q] = 0.0f;
+  const float rl0 = (float)(warp * BP2_RY);
+
+  bool ok = true;
+  for (int c = 0; c < nchunk; ++c) {
+    if (c + 1 < nchunk) angle_consts(c + 1);
+    if (!dc::mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1, a.err)) ok = false;
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+    const float *st = smem + (c & 1) * stage_sz;
+    int nm = min(BP2_MC, a.n_mu - c * BP2_MC);
+    for (int mi = 0; mi < nm; ++mi) {
+      const BPMu M = bmu[c & 1][mi];
+      const float *row = st + mi * rstride + PADL + (int)M.I00;
+      float lo = -1.0f - M.I00, hi = (float)a.n_s - M.I00;
+      float w1c = 1.0f - M.winv;
+#pragma unroll
+      for (int ry = 0; ry < BP2_RY; ++ry) {
+        float rt = fmaf(rl0 + (float)ry, M.Bs, M.F00);
+#pragma unroll
+        for (int q = 0; q < BP2_NQ; ++q) {
+          float xi = fmaf((float)(lane + 32 * q), M.Bc, rt);
+          xi = fminf(fmaxf(xi, lo), hi);
+          float f;
+          int k = dc::floor_frac(xi, f);
+          const float *p = row + k;
+          float w0 = fmaxf(0.0f, fmaf(-f, M.winv, 1.0f));
+          float w1 = fmaxf(0.0f, fmaf(f, M.winv, w1c));
+          acc[ry][q] = fmaf(w0, p[0], fmaf(w1, p[1], acc[ry][q]));
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && c + 2 < nchunk) issue(c + 2);
+  }
+  if (!ok) {
+    for (int s = 0; s < 2; ++s) dc::mbar_wait_bounded(&bars[s], 0, nullptr);
+    return;
+  }
+
+  float lmax = 0.0f;
+#pragma unroll
+  for (int ry = 0; ry < BP2_RY; ++ry) {
+    int r = r0 + warp * BP2_RY + ry;
+#pragma unroll
+    for (int q = 0; q < BP2_NQ; ++q) {
+      int j = j0 + lane + 32 * q;
+      if (r >= a.H || j >= a.W) continue;
+      float val = acc[ry][q];
+      if (a.weight != WT_NONE) {
+        float x = (j - fv.cu) * a.pitch, y = (r - fv.cv) * a.pitch;
+        float l2 = fmaf(x, x, fmaf(y, y, fv.D * fv.D));
+        val *= (a.weight == WT_D) ? l2 : fv.D * rsqrtf(l2);
+      }
+      if (a.out_kind == OUT_F32_ABSMAX) {
+        ((float *)a.out)[((size_t)n * a.H + r) * a.Wp + j] = val;
+        lmax = fmaxf(lmax, fabsf(val));
+      } else {
+        size_t o = (((size_t)b * a.V + v) * a.H + r) * a.W + j;
+        if (a.out_kind == OUT_BF16)
+          ((__nv_bfloat16 *)a.out)[o] = __float2bfloat16_rn(val);
+        else
+          ((float *)a.out)[o] = val;
+      }
+    }
+  }
+  if (a.out_kind == OUT_F32_ABSMAX) {
+    for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if (lane == 0) atomicMax(&a.absmax[n], __float_as_uint(lmax));
+  }
+}
+
+// FP16 storage with a per-view power-of-two scale chosen from the absmax so
+// that the largest value maps into [2^14, 2^15): g^F = half * scale.
+__global__ void k_to_f16(const float *__restrict__ src, const unsigned *__restrict__ absmax,
+                         int H, int W, int Wp, int V, int B, int v0, int b0,
+                         __half *__restrict__ dst, float *__restrict__ scale) {
+  int n = blockIdx.y;
+  int v = v0 + n / B, b = b0 + n % B;
+  float am = __uint_as_float(absmax[n]);
+  float sc = 1.0f;
+  if (am > 0.0f) {
+    int e;
+    frexpf(am, &e);          // am = m * 2^e, m in [0.5, 1)
+    sc = ldexpf(1.0f, e - 15);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) scale[(size_t)b * V + v] = sc;
+  float inv = 1.0f / sc;     // exact: power of two
+  size_t np = (size_t)H * W;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < np;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int r = (int)(i / W), j = (int)(i % W);
+    float val = src[((size_t)n * H + r) * Wp + j] * inv;
+    dst[((size_t)b * V + v) * np + i] = __float2half_rn(val);
+  }
+}
+
+// sum over the batch of the per-image dL/dW contributions (fixed order)
+__global__ void k_reduce_gradW(const float *__restrict__ sinoA, int n_mu, int n_s, int NSp,
+                               int B, int v0, int nv, int accumulate,
+                               float *__restrict__ gradW) {
+  size_t total = (size_t)nv * n_mu * n_s;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int k = (int)(i % n_s);
+    size_t t = i / n_s;
+    int m = (int)(t % n_mu);
+    int vl = (int)(t / n_mu);
+    float s = 0.0f;
+    for (int b = 0; b < B; ++b) s += sinoA[(((size_t)vl * B + b) * n_mu + m) * NSp + k];
+    size_t o = ((size_t)(v0 + vl) * n_mu + m) * n_s + k;
+    gradW[o] = accumulate ? gradW[o] + s : s;
+  }
+}
+
+// copy a user sinogram [B][V][n_mu][n_s] into the padded work layout, times
+// the Joseph scale of each angle (for the transpose gather)
+__global__ void k_sino_in(const float *__restrict__ R, const dc::MuRec *__restrict__ mu,
+                          int n_mu, int n_s, int NSp, int V, int B, int v0, int b0,
+                          float *__restrict__ dst) {
+  int n = blockIdx.y;
+  int v = v0 + n / B, b = b0 + n % B;
+  size_t total = (size_t)n_mu * NSp;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int m = (int)(i / NSp), k = (int)(i % NSp);
+    float val = 0.0f;
+    if (k < n_s) val = R[(((size_t)b * V + v) * n_mu + m) * n_s + k] * mu[m].jscale;
+    dst[(size_t)n * total + i] = val;
+  }
+}
+
+int round4(int x) { return (x + 3) & ~3; }
+
+size_t linesum_smem(const dc_geometry *g) {
+  int lenp = std::max(g->Wp, g->Hp);
+  return (size_t)(2 * LS_RB * (lenp + PADL + PADR) + g->mg * g->NSp) * sizeof(float);
+}
+
+size_t bp2d_smem(const dc_geometry *g) {
+  return (size_t)(2 * BP2_MC * (g->NSp + PADL + PADR)) * sizeof(float);
+}
+
+template <int MODE>
+int launch_linesum(const dc_geometry *g, LineArgs &a, cudaStream_t st) {
+  size_t sm = linesum_smem(g);
+  static bool attr_done = false;  // per template instance
+  if (!attr_done) {
+    DC_CUDA(cudaFuncSetAttribute(k_linesum<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    attr_done = true;
+  }
+  dim3 grid(g->n_groups, a.n_img);
+  dc::ProfScope ps(dc::KID_LINESUM, st);
+  k_linesum<MODE><<<grid, LS_THREADS, sm, st>>>(a);
+  DC_CHECK_LAUNCH("k_linesum");
+  return DC_OK;
+}
+
+int launch_bp2d(const dc_geometry *g, BP2Args &a, cudaStream_t st) {
+  size_t sm = bp2d_smem(g);
+  static bool attr_done = false;
+  if (!attr_done) {
+    DC_CUDA(cudaFuncSetAttribute(k_bp2d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    attr_done = true;
+  }
+  dim3 grid((a.W + BP2_TX - 1) / BP2_TX, (a.H + BP2_TY - 1) / BP2_TY, a.n_img);
+  dc::ProfScope ps(dc::KID_BP2D, st);
+  k_bp2d<<<grid, BP2_THREADS, sm, st>>>(a);
+  DC_CHECK_LAUNCH("k_bp2d");
+  return DC_OK;
+}
+
+int launch_prep(const dc_geometry *g, const float *src, int weight, int v0, int n_img, int B,
+                int b0, cudaStream_t st) {
+  const dc_geometry_desc &d = g->d;
+  PrepArgs p;
+  p.src = src;
+  p.img = g->w_img;
+  p.imgT = g->w_imgT;
+  p.fv = g->fv;
+  p.H = d.det_rows;
+  p.W = d.det_cols;
+  p.Wp = g->Wp;
+  p.Hp = g->Hp;
+  p.V = d.n_views;
+  p.B = B;
+  p.v0 = v0;
+  p.b0 = b0;
+  p.Bt = 0;
+  p.n_img = n_img;
+  p.pitch = (float)d.pitch;
+  p.weight = weight;
+  dim3 grid((std::max(g->Wp, d.det_cols) + 31) / 32, (std::max(g->Hp, d.det_rows) + 31) / 32,
+            n_img);
+  dc::ProfScope ps(dc::KID_PREP, st);
+  k_prep<<<grid, dim3(32, 8), 0, st>>>(p);
+  DC_CHECK_LAUNCH("k_prep");
+  return DC_OK;
+}
+
+LineArgs line_args(const dc_geometry *g, int B, int v0, int b0, int n_img) {
+  const dc_geometry_desc &d = g->d;
+  LineArgs a;
+  memset(&a, 0, sizeof(a));
+  a.img = g->w_img;
+  a.imgT = g->w_imgT;
+  a.H = d.det_rows;
+  a.W = d.det_cols;
+  a.Wp = g->Wp;
+  a.Hp = g->Hp;
+  a.n_mu = d.n_mu;
+  a.n_s = d.n_s;
+  a.NSp = g->NSp;
+  a.V = d.n_views;
+  a.B = B;
+  a.v0 = v0;
+  a.b0 = b0;
+  a.n_img = n_img;
+  a.pitch = (float)d.pitch;
+  a.ds = (float)d.ds;
+  a.cT = (float)((M_PI / d.n_mu) * d.ds / (d.pitch * d.pitch));
+  a.mu = g->mu;
+  a.mu_order = g->mu_order;
+  a.groups = g->groups;
+  a.fv = g->fv;
+  a.err = g->w_flags;
+  a.mg = g->mg;
+  return a;
+}
+
+BP2Args bp2_args(const dc_geometry *g, int B, int v0, int b0, int n_img, const float *sino) {
+  const dc_geometry_desc &d = g->d;
+  BP2Args a;
+  memset(&a, 0, sizeof(a));
+  a.sino = sino;
+  a.H = d.det_rows;
+  a.W = d.det_cols;
+  a.n_mu = d.n_mu;
+  a.n_s = d.n_s;
+  a.NSp = g->NSp;
+  a.V = d.n_views;
+  a.B = B;
+  a.v0 = v0;
+  a.b0 = b0;
+  a.n_img = n_img;
+  a.pitch = (float)d.pitch;
+  a.ds = (float)d.ds;
+  a.fv = g->fv;
+  a.Wp = g->Wp;
+  a.absmax = g->w_absmax;
+  a.err = g->w_flags;
+  return a;
+}
+
+int check_common(const dc_geometry *g, int B, const char *who) {
+  if (!g) return dc::fail(DC_ERR_ARG, std::string(who) + ": NULL geometry");
+  if (B < 1) return dc::fail(DC_ERR_ARG, std::string(who) + ": batch must be >= 1");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != g->device)
+    return dc::fail(DC_ERR_ARG, std::string(who) + ": geometry belongs to another device");
+  return DC_OK;
+}
+
+// A chunk holds bc batch items of cv views (bc * cv <= chunk_images images).
+struct Chunking {
+  int bc, cv;
+};
+Chunking chunking(const dc_geometry *g, int B, int view_limit = 0) {
+  Chunking c;
+  c.bc = std::min(B, g->chunk_images);
+  c.cv = std::max(1, g->chunk_images / c.bc);
+  if (view_limit > 0) c.cv = std::min(c.cv, view_limit);
+  return c;
+}
+
+}  // namespace
+
+namespace dc {
+
+int alloc_workspace(dc_geometry *g) {
+  const dc_geometry_desc &d = g->d;
+  g->Wp = round4(d.det_cols);
+  g->Hp = round4(d.det_rows);
+  g->NSp = round4(d.n_s);
+  g->img_stride = (size_t)d.det_rows * g->Wp;
+  g->imgT_stride = (size_t)d.det_cols * g->Hp;
+  g->sino_stride = (size_t)d.n_mu * g->NSp;
+  size_t per_img = (g->img_stride + g->imgT_stride + 2 * g->sino_stride) * sizeof(float);
+  // keep one chunk's work area near 48 MB so that it stays resident in L2
+  long target = 48L << 20;
+  const char *env = getenv("DC_CHUNK_IMAGES");
+  int ci = env ? atoi(env) : (int)(target / (long)per_img);
+  if (ci < 4) ci = 4;
+  if (ci > 256) ci = 256;
+  g->chunk_images = ci;
+  if (linesum_smem(g) > 200 * 1024 || bp2d_smem(g) > 200 * 1024)
+    return fail(DC_ERR_UNSUPPORTED, "detector or sinogram rows too long for shared memory");
+  DC_CUDA(dmalloc((void **)&g->w_img, sizeof(float) * g->img_stride * ci));
+  DC_CUDA(dmalloc((void **)&g->w_imgT, sizeof(float) * g->imgT_stride * ci));
+  DC_CUDA(dmalloc((void **)&g->w_sinoA, sizeof(float) * g->sino_stride * ci));
+  DC_CUDA(dmalloc((void **)&g->w_sinoB, sizeof(float) * g->sino_stride * ci));
+  DC_CUDA(dmalloc((void **)&g->w_absmax, sizeof(unsigned) * ci));
+  DC_CUDA(dmalloc((void **)&g->w_flags, sizeof(unsigned) * 4));
+  DC_CUDA(cudaMemset(g->w_flags, 0, sizeof(unsigned) * 4));
+  return DC_OK;
+}
+
+}  // namespace dc
+
+extern "C" {
+
+// Every entry point walks the (batch item, view) images chunk by chunk:
+// the outer loop takes bc batch items starting at b0, the inner loop cv views
+// starting at v0; image n of a chunk is (view v0 + n / bc, item b0 + n % bc).
+
+int dc_filter(const dc_geometry *g, int B, const float *gin, const float *W, void *gF,
+              int dtype, float *gF_scale, void *stream) {
+  int rc = check_common(g, B, "dc_filter");
+  if (rc) return rc;
+  if (!gin || !gF) return dc::fail(DC_ERR_ARG, "dc_filter: NULL g or gF");
+  if (dtype != DC_F32 && dtype != DC_BF16 && dtype != DC_F16)
+    return dc::fail(DC_ERR_ARG, "dc_filter: unknown dtype");
+  if (dtype == DC_F16 && !gF_scale)
+    return dc::fail(DC_ERR_ARG, "dc_filter: DC_F16 needs gF_scale");
+  const dc_geometry_desc &d = g->d;
+  if (d.ds < d.pitch * (1.0 - 1e-12))
+    return dc::fail(DC_ERR_UNSUPPORTED, "dc_filter: ds < pitch is not supported");
+  cudaStream_t st = (cudaStream_t)stream;
+  Chunking ck = chunking(g, B);
+  for (int b0 = 0; b0 < B; b0 += ck.bc) {
+    int bc = std::min(ck.bc, B - b0);
+    for (int v0 = 0; v0 < d.n_views; v0 += ck.cv) {
+      int nv = std::min(ck.cv, d.n_views - v0);
+      int n_img = nv * bc;
+      if ((rc = launch_prep(g, gin, WT_COS, v0, n_img, bc, b0, st))) return rc;
+      LineArgs la = line_args(g, bc, v0, b0, n_img);
+      la.Wred = W;
+      la.out = g->w_sinoA;
+      if ((rc = launch_linesum<M_FILTER>(g, la, st))) return rc;
+      BP2Args ba = bp2_args(g, bc, v0, b0, n_img, g->w_sinoA);
+      ba.weight = WT_D;
+      if (dtype == DC_F16) {
+        DC_CUDA(cudaMemsetAsync(g->w_absmax, 0, sizeof(unsigned) * n_img, st));
+        ba.out_kind = OUT_F32_ABSMAX;
+        ba.out = g->w_img;
+        if ((rc = launch_bp2d(g, ba, st))) return rc;
+        dim3 grid(64, n_img);
+        dc::ProfScope ps(dc::KID_TO_F16, st);
+        k_to_f16<<<grid, 256, 0, st>>>(g->w_img, g->w_absmax, d.det_rows, d.det_cols, g->Wp,
+                                       d.n_views, bc, v0, b0, (__half *)gF, gF_scale);
+        DC_CHECK_LAUNCH("k_to_f16");
+      } else {
+        ba.out_kind = (dtype == DC_BF16) ? OUT_BF16 : OUT_F32;
+        ba.out = gF;
+        if ((rc = launch_bp2d(g, ba, st))) return rc;
+      }
+    }
+  }
+  return DC_OK;
+}
+
+int dc_filter_adjoint(const dc_geometry *g, int B, const float *grad_gF, const float *gin,
+                      const float *W, float *grad_g, float *grad_W, int view_chunk,
+                      void *stream) {
+  int rc = check_common(g, B, "dc_filter_adjoint");
+  if (rc) return rc;
+  if (!grad_gF || !gin) return dc::fail(DC_ERR_ARG, "dc_filter_adjoint: NULL grad_gF or g");
+  if (view_chunk < 0) return dc::fail(DC_ERR_ARG, "dc_filter_adjoint: negative view_chunk");
+  const dc_geometry_desc &d = g->d;
+  if (d.ds < d.pitch * (1.0 - 1e-12))
+    return dc::fail(DC_ERR_UNSUPPORTED, "dc_filter_adjoint: ds < pitch is not supported");
+  if (!grad_g && !grad_W) return DC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Chunking ck = chunking(g, B, view_chunk);
+  for (int b0 = 0; b0 < B; b0 += ck.bc) {
+    int bc = std::min(ck.bc, B - b0);
+    for (int v0 = 0; v0 < d.n_views; v0 += ck.cv) {
+      int nv = std::min(ck.cv, d.n_views - v0);
+      int n_img = nv * bc;
+      // dL/dP up to D_b^T: line differences of w_d * dL/dg^F
+      if ((rc = launch_prep(g, grad_gF, WT_D, v0, n_img, bc, b0, st))) return rc;
+      LineArgs la = line_args(g, bc, v0, b0, n_img);
+      la.Wred = W;
+      la.sinoA = g->w_sinoA;
+      la.sinoB = g->w_sinoB;
+      if ((rc = launch_linesum<M_DIFFSTORE>(g, la, st))) return rc;
+      // recompute S from w_cos * g and finish the chain
+      if ((rc = launch_prep(g, gin, WT_COS, v0, n_img, bc, b0, st))) return rc;
+      if ((rc = launch_linesum<M_ADJ>(g, la, st))) return rc;
+      if (grad_W) {
+        size_t total = (size_t)nv * d.n_mu * d.n_s;
+        int nb = (int)std::min<size_t>((total + 255) / 256, 4096);
+        dc::ProfScope ps(dc::KID_REDUCE_W, st);
+        k_reduce_gradW<<<nb, 256, 0, st>>>(g->w_sinoA, d.n_mu, d.n_s, g->NSp, bc, v0, nv,
+                                           b0 > 0, grad_W);
+        DC_CHECK_LAUNCH("k_reduce_gradW");
+      }
+      if (grad_g) {
+        BP2Args ba = bp2_args(g, bc, v0, b0, n_img, g->w_sinoB);
+        ba.weight = WT_COS;
+        ba.out_kind = OUT_F32;
+        ba.out = grad_g;
+        if ((rc = launch_bp2d(g, ba, st))) return rc;
+      }
+    }
+  }
+  return DC_OK;
+}
+
+int dc_grangeat(const dc_geometry *g, int B, const float *gin, float *S, void *stream) {
+  int rc = check_common(g, B, "dc_grangeat");
+  if (rc) return rc;
+  if (!gin || !S) return dc::fail(DC_ERR_ARG, "dc_grangeat: NULL argument");
+  const dc_geometry_desc &d = g->d;
+  cudaStream_t st = (cudaStream_t)stream;
+  Chunking ck = chunking(g, B);
+  for (int b0 = 0; b0 < B; b0 += ck.bc) {
+    int bc = std::min(ck.bc, B - b0);
+    for (int v0 = 0; v0 < d.n_views; v0 += ck.cv) {
+      int n_img = std::min(ck.cv, d.n_views - v0) * bc;
+      if ((rc = launch_prep(g, gin, WT_COS, v0, n_img, bc, b0, st))) return rc;
+      LineArgs la = line_args(g, bc, v0, b0, n_img);
+      la.out = S;
+      if ((rc = launch_linesum<M_GRANGEAT>(g, la, st))) return rc;
+    }
+  }
+  return DC_OK;
+}
+
+int dc_radon2d(const dc_geometry *g, int B, const float *img, float *R, void *stream) {
+  int rc = check_common(g, B, "dc_radon2d");
+  if (rc) return rc;
+  if (!img || !R) return dc::fail(DC_ERR_ARG, "dc_radon2d: NULL argument");
+  const dc_geometry_desc &d = g->d;
+  cudaStream_t st = (cudaStream_t)stream;
+  Chunking ck = chunking(g, B);
+  for (int b0 = 0; b0 < B; b0 += ck.bc) {
+    int bc = std::min(ck.bc, B - b0);
+    for (int v0 = 0; v0 < d.n_views; v0 += ck.cv) {
+      int n_img = std::min(ck.cv, d.n_views - v0) * bc;
+      if ((rc = launch_prep(g, img, WT_NONE, v0, n_img, bc, b0, st))) return rc;
+      LineArgs la = line_args(g, bc, v0, b0, n_img);
+      la.out = R;
+      if ((rc = launch_linesum<M_RAW>(g, la, st))) return rc;
+    }
+  }
+  return DC_OK;
+}
+
+int dc_radon2d_adjoint(const dc_geometry *g, int B, const float *R, float *img, void *stream) {
+  int rc = check_common(g, B, "dc_radon2d_adjoint");
+  if (rc) return rc;
+  if (!img || !R) return dc::fail(DC_ERR_ARG, "dc_radon2d_adjoint: NULL argument");
+  const dc_geometry_desc &d = g->d;
+  if (d.ds < d.pitch * (1.0 - 1e-12))
+    return dc::fail(DC_ERR_UNSUPPORTED, "dc_radon2d_adjoint: ds < pitch is not supported");
+  cudaStream_t st = (cudaStream_t)stream;
+  Chunking ck = chunking(g, B);
+  for (int b0 = 0; b0 < B; b0 += ck.bc) {
+    int bc = std::min(ck.bc, B - b0);
+    for (int v0 = 0; v0 < d.n_views; v0 += ck.cv) {
+      int n_img = std::min(ck.cv, d.n_views - v0) * bc;
+      dim3 grid(64, n_img);
+      dc::ProfScope ps(dc::KID_SINO_IN, st);
+      k_sino_in<<<grid, 256, 0, st>>>(R, g->mu, d.n_mu, d.n_s, g->NSp, d.n_views, bc, v0, b0,
+                                      g->w_sinoA);
+      DC_CHECK_LAUNCH("k_sino_in");
+      BP2Args ba = bp2_args(g, bc, v0, b0, n_img, g->w_sinoA);
+      ba.weight = WT_NONE;
+      ba.out_kind = OUT_F32;
+      ba.out = img;
+      if ((rc = launch_bp2d(g, ba, st))) return rc;
+    }
+  }
+  return DC_OK;
+}
+
+int dc_sync_status(const dc_geometry *g, void *stream) {
+  if (!g) return dc::fail(DC_ERR_ARG, "dc_sync_status: NULL geometry");
+  DC_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  unsigned flags = 0;
+  DC_CUDA(cudaMemcpy(&flags, g->w_flags, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (flags) {
+    DC_CUDA(cudaMemset(g->w_flags, 0, sizeof(unsigned)));
+    return dc::fail(DC_ERR_TIMEOUT, "a bounded device wait gave up");
+  }
+  return DC_OK;
+}
+
+}  // extern "C"

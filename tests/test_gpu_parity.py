@@ -1,0 +1,210 @@
+"""CUDA path versus the FP64 oracle, element by element, through the C ABI.
+
+Tolerance: 1e-4 relative L2 for FP32 results (the target the method is
+built to); tighter where no derivative amplifies rounding (line sums,
+backprojection).  Inputs are identical FP32-rounded arrays on both sides.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+from paper_2410_14900_gb300 import api
+from paper_2410_14900_gb300 import _lib as L
+
+from cases import arc_open, circle64, phantom_projections, ragged, random_weights, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+CASES = {"circle64": circle64, "ragged": ragged, "arc_open": arc_open}
+
+
+def _setup(case):
+    return api.Geometry(case.desc, case.P, case.vdl), orc.Geometry(case.desc, case.P, case.vdl)
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def prob(request):
+    case = CASES[request.param]()
+    gg, og = _setup(case)
+    g32 = phantom_projections(case).astype(np.float32)
+    W32 = random_weights(case).astype(np.float32)
+    return dict(case=case, gpu=gg, orc=og, g=g32, W=W32)
+
+
+def test_geometry_matches_oracle(prob):
+    v = api.dc_get_view_geometry(prob["gpu"])
+    og = prob["orc"]
+    for i in range(prob["case"].desc["n_views"]):
+        np.testing.assert_allclose(v[i, 0:3], og.source(i), rtol=0, atol=1e-9)
+        lx, ly, lz = og.frame(i)
+        np.testing.assert_allclose(v[i, 3:6], lx, atol=1e-13)
+        np.testing.assert_allclose(v[i, 6:9], ly, atol=1e-13)
+        np.testing.assert_allclose(v[i, 9:12], lz, atol=1e-13)
+        assert abs(v[i, 12] - og.D(i)) < 1e-9
+        np.testing.assert_allclose(v[i, 13:15], og.principal_point(i), atol=1e-9)
+        np.testing.assert_allclose(v[i, 15:18], og.tangent(i), rtol=1e-12, atol=1e-9)
+
+
+def test_radon2d_matches_oracle(prob):
+    case, og = prob["case"], prob["orc"]
+    d = case.desc
+    rng = np.random.default_rng(1)
+    img = rng.normal(size=(case.B, d["n_views"], d["det_rows"], d["det_cols"])).astype(np.float32)
+    R = _host(api.dc_radon2d(prob["gpu"], _dev(img)))
+    for b in range(case.B):
+        for i in range(0, d["n_views"], max(1, d["n_views"] // 5)):
+            cu, cv = og.principal_point(i)
+            ref = orc.radon(img[b, i], d["pitch"], d["n_mu"], d["n_s"], d["ds"], cu, cv)
+            assert rel_l2(R[b, i], ref) < 2e-6
+
+
+def test_radon2d_adjoint_matches_oracle(prob):
+    case, og = prob["case"], prob["orc"]
+    d = case.desc
+    rng = np.random.default_rng(2)
+    R = rng.normal(size=(case.B, d["n_views"], d["n_mu"], d["n_s"])).astype(np.float32)
+    img = _host(api.dc_radon2d_adjoint(prob["gpu"], _dev(R)))
+    for b in range(case.B):
+        for i in range(0, d["n_views"], max(1, d["n_views"] // 5)):
+            cu, cv = og.principal_point(i)
+            ref = orc.radon_T(R[b, i], d["det_rows"], d["det_cols"], d["pitch"], d["ds"], cu, cv)
+            assert rel_l2(img[b, i], ref) < 1e-5
+
+
+def test_grangeat_matches_oracle(prob):
+    case, og = prob["case"], prob["orc"]
+    S = _host(api.dc_grangeat(prob["gpu"], _dev(prob["g"])))
+    errs = []
+    for b in range(case.B):
+        for i in range(case.desc["n_views"]):
+            errs.append(rel_l2(S[b, i], orc.grangeat(og, i, prob["g"][b, i])))
+    assert max(errs) < 1e-4, max(errs)
+
+
+def test_filter_matches_oracle(prob):
+    case = prob["case"]
+    W = prob["W"] if case.name != "circle64" else None
+    gF, _ = api.dc_filter(prob["gpu"], _dev(prob["g"]), None if W is None else _dev(W))
+    ref = orc.filter(prob["orc"], prob["g"], W)
+    err = rel_l2(_host(gF), ref)
+    assert err < 1e-4, err
+
+
+def test_backproject_matches_oracle(prob):
+    case = prob["case"]
+    d = case.desc
+    rng = np.random.default_rng(3)
+    gF = rng.normal(size=(case.B, d["n_views"], d["det_rows"], d["det_cols"])).astype(np.float32)
+    ref = orc.backproject(prob["orc"], gF)
+    for kahan in (False, True):
+        vol = _host(api.dc_backproject(prob["gpu"], _dev(gF), kahan=kahan))
+        assert rel_l2(vol, ref) < 1e-5
+    relu = _host(api.dc_backproject(prob["gpu"], _dev(gF), relu=True))
+    assert rel_l2(relu, np.maximum(ref, 0)) < 1e-5
+    base = _dev(ref)
+    acc = _host(api.dc_backproject(prob["gpu"], _dev(gF), out=base, accum=True))
+    assert rel_l2(acc, 2 * ref) < 1e-5
+
+
+def test_reconstruction_matches_oracle(prob):
+    case = prob["case"]
+    W = prob["W"] if case.name != "circle64" else None
+    vol = api.reconstruct(prob["gpu"], _dev(prob["g"]), None if W is None else _dev(W))
+    ref = orc.reconstruct(prob["orc"], prob["g"], W)
+    err = rel_l2(_host(vol), ref)
+    assert err < 1e-4, err
+
+
+def test_backproject_adjoint_matches_oracle(prob):
+    case = prob["case"]
+    d = case.desc
+    rng = np.random.default_rng(4)
+    gv = rng.normal(size=(case.B, d["vol_z"], d["vol_y"], d["vol_x"])).astype(np.float32)
+    out = _host(api.dc_backproject_adjoint(prob["gpu"], _dev(gv)))
+    ref = orc.backproject_adjoint(prob["orc"], gv)
+    assert rel_l2(out, ref) < 1e-5
+    # ReLU mask: zero gradient where the forward output was clamped
+    mask = rng.normal(size=gv.shape).astype(np.float32)
+    out2 = _host(api.dc_backproject_adjoint(prob["gpu"], _dev(gv), relu_vol=_dev(mask)))
+    ref2 = orc.backproject_adjoint(prob["orc"], gv * (mask > 0))
+    assert rel_l2(out2, ref2) < 1e-5
+
+
+def test_filter_adjoint_matches_oracle(prob):
+    case = prob["case"]
+    d = case.desc
+    rng = np.random.default_rng(6)
+    G = rng.normal(size=(case.B, d["n_views"], d["det_rows"], d["det_cols"])).astype(np.float32)
+    W = prob["W"]
+    gg, gW = api.dc_filter_adjoint(prob["gpu"], _dev(G), _dev(prob["g"]), _dev(W))
+    rg, rW = orc.filter_adjoint(prob["orc"], prob["g"], G, W)
+    assert rel_l2(_host(gg), rg) < 1e-4
+    assert rel_l2(_host(gW), rW) < 1e-4
+    # view chunking does not change the result
+    gg2, gW2 = api.dc_filter_adjoint(prob["gpu"], _dev(G), _dev(prob["g"]), _dev(W),
+                                     view_chunk=3)
+    assert rel_l2(_host(gg2), _host(gg)) < 1e-6
+    assert rel_l2(_host(gW2), _host(gW)) < 1e-6
+
+
+def test_low_precision_storage_error_is_bounded(prob):
+    """BF16 / FP16 storage of g^F with FP32 interpolation (error vs FP64 stated)."""
+    case = prob["case"]
+    ref = orc.reconstruct(prob["orc"], prob["g"], None)
+    g = _dev(prob["g"])
+    errs = {}
+    for dt in ("bf16", "f16"):
+        gF, sc = api.dc_filter(prob["gpu"], g, None, dtype=dt)
+        for kahan in (False, True):
+            vol = api.dc_backproject(prob["gpu"], gF, sc, kahan=kahan)
+            errs[(dt, kahan)] = rel_l2(_host(vol), ref)
+    print(case.name, errs)
+    assert errs[("bf16", True)] < 1e-2
+    assert errs[("f16", True)] < 2e-3
+    api.dc_sync_status(prob["gpu"])
+
+
+def test_argument_errors_on_gpu():
+    case = circle64()
+    gg = api.Geometry(case.desc, case.P, case.vdl)
+    Lh = L.load()
+    x = torch.zeros(1, device="cuda")
+    p = x.data_ptr()
+    assert Lh.dc_filter(gg.handle, 0, p, None, p, 0, None, None) == L.DC_ERR_ARG
+    assert Lh.dc_filter(gg.handle, 1, p, None, p, 7, None, None) == L.DC_ERR_ARG
+    assert Lh.dc_filter(gg.handle, 1, p, None, p, L.DC_F16, None, None) == L.DC_ERR_ARG
+    assert Lh.dc_backproject(gg.handle, 1, p, 0, None, p, 64, None) == L.DC_ERR_ARG
+    bad = dict(case.desc, ds=case.desc["pitch"] * 0.5)
+    g2 = api.Geometry(bad, case.P, case.vdl)
+    assert Lh.dc_filter(g2.handle, 1, p, None, p, 0, None, None) == L.DC_ERR_UNSUPPORTED
+    with pytest.raises(L.DCError):
+        api.Geometry(case.desc, case.P * np.array([1, 1.5, 1, 1])[None, None, :], case.vdl)
+    api.dc_sync_status(gg)
+
+
+def test_allocation_failure_is_reported():
+    case = circle64()
+    Lh = L.load()
+    for n in range(0, 64):
+        Lh.dc_debug_fail_alloc_after(n)
+        try:
+            g = api.Geometry(case.desc, case.P, case.vdl)
+        except L.DCError as e:
+            assert e.code == L.DC_ERR_OOM
+            continue
+        finally:
+            Lh.dc_debug_fail_alloc_after(-1)
+        g.close()
+        break
+    else:
+        pytest.fail("setup never succeeded")
