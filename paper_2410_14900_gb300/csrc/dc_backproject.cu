@@ -9,8 +9,10 @@
 // a voxel costs one reciprocal for the depth and one for the distance
 // weight.  Coordinates are taken relative to the volume centre and to the
 // principal point so that FP32 keeps ~1e-5 pixel accuracy.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cstring>
@@ -217,6 +219,314 @@ __global__ void __launch_bounds__(BP_TX *BP_TY) k_bp3d_adj(BPAdjArgs a) {
   }
 }
 
+
+// ------------------------------------------------------------------------
+// Shared-memory staged backprojection.  A CTA owns a 16 x 16 x 32 voxel box.
+// For every view the box's eight corners are projected; the bounding box of
+// the projections (plus a one-pixel margin) is the footprint of every voxel
+// of the box on the detector.  A tiled TMA load copies that footprint
+// (a 32x48 or 64x48 box, zero outside the detector) into shared memory
+// through a three-stage mbarrier pipeline, and the voxels interpolate from
+// shared memory without bounds checks.  Footprints are computed for 32 views
+// at a time, one corner per thread.  Views whose footprint does not fit (or
+// whose box reaches behind the source) fall back to bounds-checked global
+// loads; views whose footprint misses the detector are skipped.
+constexpr int TB_TX = 16, TB_TY = 16, TB_NZ = 32;
+constexpr int TB_BWN = 32, TB_BWW = 64, TB_BH = 48;
+constexpr int TB_NS = 3;
+constexpr int TB_VCH = 32;
+enum { FP_GLOBAL = 0, FP_NARROW = 1, FP_WIDE = 2, FP_SKIP = 3 };
+
+template <typename T>
+__device__ __forceinline__ float sld(const T *p);
+template <>
+__device__ __forceinline__ float sld<float>(const float *p) { return *p; }
+template <>
+__device__ __forceinline__ float sld<__nv_bfloat16>(const __nv_bfloat16 *p) {
+  return __bfloat162float(*p);
+}
+template <>
+__device__ __forceinline__ float sld<__half>(const __half *p) { return __half2float(*p); }
+
+template <typename T, bool KAHAN>
+__global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_tma(BPArgs a, unsigned *err,
+                                                          const __grid_constant__ CUtensorMap tmn,
+                                                          const __grid_constant__ CUtensorMap tmw) {
+  __shared__ __align__(128) unsigned char sbuf[TB_NS][TB_BH * TB_BWW * sizeof(T)];
+  __shared__ uint64_t full[TB_NS];
+  __shared__ dc::BPView sv[TB_VCH];
+  __shared__ int4 vtab[TB_VCH];
+
+  const int tid = threadIdx.y * TB_TX + threadIdx.x;
+  const int ix = blockIdx.x * TB_TX + threadIdx.x;
+  const int iy = blockIdx.y * TB_TY + threadIdx.y;
+  const int zblocks = (a.nz + TB_NZ - 1) / TB_NZ;
+  const int b = blockIdx.z / zblocks;
+  const int z0 = (blockIdx.z % zblocks) * TB_NZ;
+  const float cx = 0.5f * (float)(a.nx - 1), cy = 0.5f * (float)(a.ny - 1),
+              cz = 0.5f * (float)(a.nz - 1);
+  const float xo = ((float)ix - cx) * a.dx;
+  const float yo = ((float)iy - cy) * a.dy;
+  const float zo = ((float)z0 - cz) * a.dz;
+  // extremal voxel centres of this CTA's box (clipped to the volume)
+  const float bx0 = ((float)(blockIdx.x * TB_TX) - cx) * a.dx;
+  const float bx1 = ((float)min(blockIdx.x * TB_TX + TB_TX - 1, a.nx - 1) - cx) * a.dx;
+  const float by0 = ((float)(blockIdx.y * TB_TY) - cy) * a.dy;
+  const float by1 = ((float)min(blockIdx.y * TB_TY + TB_TY - 1, a.ny - 1) - cy) * a.dy;
+  const float bz0 = zo;
+  const float bz1 = ((float)min(z0 + TB_NZ - 1, a.nz - 1) - cz) * a.dz;
+  const size_t np = (size_t)a.H * a.W;
+  const T *gbase = (const T *)a.gF + (size_t)b * a.V * np;
+
+  if (tid == 0) {
+    for (int q = 0; q < TB_NS; ++q) dc::mbar_init(&full[q], 1);
+    dc::fence_barrier_init();
+  }
+  float acc[TB_NZ], cmp[TB_NZ];
+#pragma unroll
+  for (int k = 0; k < TB_NZ; ++k) acc[k] = cmp[k] = 0.0f;
+
+  unsigned it = 0;  // running view counter: stage it % NS, parity (it / NS) & 1
+  bool ok = true;
+  for (int c0 = 0; c0 < a.V && ok; c0 += TB_VCH) {
+    const int nvc = min(TB_VCH, a.V - c0);
+    __syncthreads();
+    {  // footprints of this chunk: thread = (view, corner)
+      const int vi = tid >> 3, cr = tid & 7;
+      float umin = 0.0f, umax = 0.0f, vmin = 0.0f, vmax = 0.0f;
+      int good = 1;
+      if (vi < nvc) {
+        const dc::BPView w = a.views[c0 + vi];
+        if (cr == 0) sv[vi] = w;
+        float X = (cr & 1) ? bx1 : bx0, Y = (cr & 2) ? by1 : by0, Z = (cr & 4) ? bz1 : bz0;
+        float U = fmaf(w.r0.x, X, fmaf(w.r0.y, Y, fmaf(w.r0.z, Z, w.r0.w)));
+        float Vv = fmaf(w.r1.x, X, fmaf(w.r1.y, Y, fmaf(w.r1.z, Z, w.r1.w)));
+        float Wd = fmaf(w.r2.x, X, fmaf(w.r2.y, Y, fmaf(w.r2.z, Z, w.r2.w)));
+        good = (Wd > 1.0f);
+        float u = good ? U / Wd + w.pp.x : 0.0f, v = good ? Vv / Wd + w.pp.y : 0.0f;
+        umin = umax = u;
+        vmin = vmax = v;
+      }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, o));
+        umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        good &= __shfl_xor_sync(0xffffffffu, good, o);
+      }
+      if (vi < nvc && cr == 0) {
+        int4 t = make_int4(0, 0, FP_GLOBAL, TB_BWW);
+        if (good && fabsf(umin) < 1e6f && fabsf(umax) < 1e6f && fabsf(vmin) < 1e6f &&
+            fabsf(vmax) < 1e6f) {
+          constexpr int ALIGN = 16 / (int)sizeof(T);  // TMA x offset: 16-byte multiple
+          int j0 = (int)floorf(umin) - 1, j1 = (int)floorf(umax) + 2;
+          int r0 = (int)floorf(vmin) - 1, r1 = (int)floorf(vmax) + 2;
+          int x0 = j0 & ~(ALIGN - 1);
+          int ncol = j1 - x0 + 1, nrow = r1 - r0 + 1;
+          if (j1 < 0 || x0 >= a.W || r1 < 0 || r0 >= a.H) {
+            t = make_int4(x0, r0, FP_SKIP, TB_BWW);
+          } else if (nrow <= TB_BH && ncol <= TB_BWN) {
+            t = make_int4(x0, r0, FP_NARROW, TB_BWN);
+          } else if (nrow <= TB_BH && ncol <= TB_BWW) {
+            t = make_int4(x0, r0, FP_WIDE, TB_BWW);
+          }
+        }
+        vtab[vi] = t;
+      }
+    }
+    __syncthreads();
+    auto issue = [&](int vi, unsigned s) {
+      const int4 t = vtab[vi];
+      dc::fence_proxy_async();
+      if (t.z == FP_NARROW) {
+        dc::mbar_arrive_expect_tx(&full[s], TB_BWN * TB_BH * sizeof(T));
+        dc::tma_load_3d(sbuf[s], &tmn, t.x, t.y, b * a.V + c0 + vi, &full[s]);
+      } else if (t.z == FP_WIDE) {
+        dc::mbar_arrive_expect_tx(&full[s], TB_BWW * TB_BH * sizeof(T));
+        dc::tma_load_3d(sbuf[s], &tmw, t.x, t.y, b * a.V + c0 + vi, &full[s]);
+      } else {
+        dc::mbar_arrive(&full[s]);
+      }
+    };
+    if (tid == 0)
+      for (int q = 0; q < TB_NS - 1 && q < nvc; ++q) issue(q, (it + q) % TB_NS);
+
+    for (int vi = 0; vi < nvc; ++vi, ++it) {
+      const unsigned s = it % TB_NS;
+      const int4 t = vtab[vi];
+      bool w_ok = dc::mbar_wait_bounded(&full[s], (it / TB_NS) & 1, err);
+      if (__syncthreads_or(!w_ok)) {
+        ok = false;
+        break;
+      }
+      const dc::BPView w = sv[vi];
+      const int i = c0 + vi;
+      float sc = 1.0f;
+      if (a.scale) sc = a.scale[(size_t)b * a.V + i];
+      float U0 = fmaf(w.r0.x, xo, fmaf(w.r0.y, yo, fmaf(w.r0.z, zo, w.r0.w)));
+      float V0 = fmaf(w.r1.x, xo, fmaf(w.r1.y, yo, fmaf(w.r1.z, zo, w.r1.w)));
+      float W0 = fmaf(w.r2.x, xo, fmaf(w.r2.y, yo, fmaf(w.r2.z, zo, w.r2.w)));
+      float dU = w.r0.z * a.dz, dV = w.r1.z * a.dz, dW = w.r2.z * a.dz;
+      float ex = w.ca.x + xo, ey = w.ca.y + yo, ez0 = w.ca.z + zo;
+      float rho2 = fmaf(ex, ex, ey * ey);
+      if (t.z == FP_NARROW || t.z == FP_WIDE) {
+        const T *tile = (const T *)sbuf[s];
+        const int stride = t.w;
+        const float cul = w.pp.x - (float)t.x, cvl = w.pp.y - (float)t.y;
+        const float umx = (float)stride - 1.001f, vmx = (float)TB_BH - 1.001f;
+        if (w.ca.w != 0.0f) {
+          // circle view: u and the depth do not change along the column
+          float rw = dc::rcp_approx(W0);
+          float u = fminf(fmaxf(fmaf(U0, rw, cul), 0.0f), umx), fu;
+          int j = dc::floor_frac(u, fu);
+          const T *col = tile + j;
+          float vb = fmaf(V0, rw, cvl), dv = dV * rw;
+#pragma unroll
+          for (int k = 0; k < TB_NZ; ++k) {
+            float kf = (float)k;
+            float v = fminf(fmaxf(fmaf(kf, dv, vb), 0.0f), vmx), fv;
+            int r = dc::floor_frac(v, fv);
+            const T *p = col + r * stride;
+            float g00 = sld(p), g01 = sld(p + 1), g10 = sld(p + stride), g11 = sld(p + stride + 1);
+            float x0 = fmaf(fu, g01 - g00, g00), x1 = fmaf(fu, g11 - g10, g10);
+            float val = fmaf(fv, x1 - x0, x0) * sc;
+            float ez = fmaf(kf, a.dz, ez0);
+            float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
+            if (KAHAN) {
+              float y = term - cmp[k];
+              float tt = acc[k] + y;
+              cmp[k] = (tt - acc[k]) - y;
+              acc[k] = tt;
+            } else {
+              acc[k] += term;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < TB_NZ; ++k) {
+            float kf = (float)k;
+            float rw = dc::rcp_approx(fmaf(kf, dW, W0));
+            float u = fminf(fmaxf(fmaf(fmaf(kf, dU, U0), rw, cul), 0.0f), umx);
+            float v = fminf(fmaxf(fmaf(fmaf(kf, dV, V0), rw, cvl), 0.0f), vmx);
+            float fu, fv;
+            int j = dc::floor_frac(u, fu), r = dc::floor_frac(v, fv);
+            const T *p = tile + r * stride + j;
+            float g00 = sld(p), g01 = sld(p + 1), g10 = sld(p + stride), g11 = sld(p + stride + 1);
+            float x0 = fmaf(fu, g01 - g00, g00), x1 = fmaf(fu, g11 - g10, g10);
+            float val = fmaf(fv, x1 - x0, x0) * sc;
+            float ez = fmaf(kf, a.dz, ez0);
+            float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
+            if (KAHAN) {
+              float y = term - cmp[k];
+              float tt = acc[k] + y;
+              cmp[k] = (tt - acc[k]) - y;
+              acc[k] = tt;
+            } else {
+              acc[k] += term;
+            }
+          }
+        }
+      } else if (t.z == FP_GLOBAL) {
+        const T *img = gbase + (size_t)i * np;
+#pragma unroll
+        for (int k = 0; k < TB_NZ; ++k) {
+          float kf = (float)k;
+          float dep = fmaf(kf, dW, W0);
+          if (!(dep > 0.0f)) continue;
+          float rw = __frcp_rn(dep);
+          float u = fmaf(fmaf(kf, dU, U0), rw, w.pp.x);
+          float v = fmaf(fmaf(kf, dV, V0), rw, w.pp.y);
+          float val = bilinear<T>(img, a.H, a.W, u, v) * sc;
+          float ez = fmaf(kf, a.dz, ez0);
+          float term = val * __frcp_rn(fmaf(ez, ez, rho2));
+          if (KAHAN) {
+            float y = term - cmp[k];
+            float tt = acc[k] + y;
+            cmp[k] = (tt - acc[k]) - y;
+            acc[k] = tt;
+          } else {
+            acc[k] += term;
+          }
+        }
+      }
+      __syncthreads();
+      if (tid == 0 && vi + TB_NS - 1 < nvc) issue(vi + TB_NS - 1, (it + TB_NS - 1) % TB_NS);
+    }
+  }
+  if (!ok) {
+    for (int q = 0; q < TB_NS; ++q) dc::mbar_wait_bounded(&full[q], 0, nullptr);
+    return;
+  }
+  if (ix >= a.nx || iy >= a.ny) return;
+  const size_t nvox = (size_t)a.nx * a.ny * a.nz;
+#pragma unroll
+  for (int k = 0; k < TB_NZ; ++k) {
+    int iz = z0 + k;
+    if (iz >= a.nz) break;
+    size_t o = (size_t)b * nvox + ((size_t)iz * a.ny + iy) * a.nx + ix;
+    float f = acc[k];
+    if (a.flags & DC_ACCUM) f += a.vol[o];
+    if ((a.flags & DC_RELU) && f < 0.0f) f = 0.0f;
+    a.vol[o] = f;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 3-D map over g^F viewed as [B*V][H][W] with a box of bw x TB_BH x 1
+bool make_map(CUtensorMap *m, const void *base, int dtype, int W, int H, long long nimg,
+              int bw) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  int es = (dtype == DC_F32) ? 4 : 2;
+  CUtensorMapDataType t = (dtype == DC_F32)    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                          : (dtype == DC_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nimg};
+  cuuint64_t strides[2] = {(cuuint64_t)W * es, (cuuint64_t)W * H * es};
+  cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)TB_BH, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, t, 3, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <typename T>
+int launch_bp_tma(const dc_geometry *g, BPArgs &a, int dtype, bool kahan, cudaStream_t st,
+                  bool *used) {
+  *used = false;
+  int es = (dtype == DC_F32) ? 4 : 2;
+  if (((size_t)a.W * es) % 16 != 0 || ((uintptr_t)a.gF & 15) != 0) return DC_OK;
+  if (getenv("DC_BP_NO_TMA")) return DC_OK;
+  CUtensorMap mn, mw;
+  long long nimg = (long long)a.B * a.V;
+  if (!make_map(&mn, a.gF, dtype, a.W, a.H, nimg, TB_BWN) ||
+      !make_map(&mw, a.gF, dtype, a.W, a.H, nimg, TB_BWW))
+    return DC_OK;
+  dim3 blk(TB_TX, TB_TY);
+  dim3 grid((a.nx + TB_TX - 1) / TB_TX, (a.ny + TB_TY - 1) / TB_TY,
+            ((a.nz + TB_NZ - 1) / TB_NZ) * a.B);
+  if (kahan)
+    k_bp3d_tma<T, true><<<grid, blk, 0, st>>>(a, g->w_flags, mn, mw);
+  else
+    k_bp3d_tma<T, false><<<grid, blk, 0, st>>>(a, g->w_flags, mn, mw);
+  *used = true;
+  return DC_OK;
+}
+
 int check_bp(const dc_geometry *g, int B, const char *who) {
   if (!g) return dc::fail(DC_ERR_ARG, std::string(who) + ": NULL geometry");
   if (B < 1) return dc::fail(DC_ERR_ARG, std::string(who) + ": batch must be >= 1");
@@ -263,6 +573,18 @@ int dc_backproject(const dc_geometry *g, int B, const void *gF, int dtype,
   cudaStream_t st = (cudaStream_t)stream;
   bool kahan = (flags & DC_KAHAN) != 0;
   dc::ProfScope ps(dc::KID_BP3D, st);
+  bool used = false;
+  switch (dtype) {
+    case DC_F32: rc = launch_bp_tma<float>(g, a, dtype, kahan, st, &used); break;
+    case DC_BF16: rc = launch_bp_tma<__nv_bfloat16>(g, a, dtype, kahan, st, &used); break;
+    case DC_F16: rc = launch_bp_tma<__half>(g, a, dtype, kahan, st, &used); break;
+    default: return dc::fail(DC_ERR_ARG, "dc_backproject: unknown dtype");
+  }
+  if (rc) return rc;
+  if (used) {
+    DC_CHECK_LAUNCH("k_bp3d_tma");
+    return DC_OK;
+  }
   switch (dtype) {
     case DC_F32:
       if (kahan) k_bp3d<float, true><<<grid, blk, 0, st>>>(a);
