@@ -211,6 +211,30 @@ int dc_radon2d_adjoint(const dc_geometry *geom, int B, const float *R, float *im
  */
 int dc_sync_status(const dc_geometry *geom, void *stream);
 
+/*
+ * dc_radon2d_noalloc -- the Joseph 2D Radon transform of dc_radon2d for
+ * callers that cannot allocate device memory: a real-time loop whose memory
+ * budget is fixed before the scan and must never wait on the driver's
+ * allocator, or a host that embeds this library inside another runtime's
+ * memory pool and cannot create a geometry handle.  The paper has no
+ * counterpart; it is an interface variant.  It allocates nothing and needs
+ * no handle: its work area is a fixed 32 MiB array compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   img   : device, [n_img][H][W] FP32 detector images (caller-owned).
+ *   R     : device, [n_img][n_mu][n_s] FP32 line sums (caller-owned).
+ *   cu, cv: principal point (column, row) shared by all images; pitch, ds,
+ *           mu_m = m pi / n_mu and s_k as for a geometry handle.
+ * Limits: n_mu <= 2048; one image needs (H * round4(W) + W * round4(H)) * 4
+ * bytes of the fixed area, at most 32 MiB - 128 KiB (larger requests return
+ * DC_ERR_ARG with the numbers); images are processed in groups that fit.
+ * The first call on a device looks up the array's device address (set-up);
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents: calls that overlap on the GPU (two
+ * streams, two threads) race on it and must be serialised by the caller.
+ */
+int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, double pitch, double ds,
+                       double cu, double cv, const float *img, float *R, void *stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *dc_status_string(int status);
 

@@ -52,6 +52,9 @@ _SIGS = {
     "dc_radon2d": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "dc_radon2d_adjoint": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "dc_sync_status": (ctypes.c_int, [_P, _P]),
+    "dc_radon2d_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, _P, _P, _P]),
     "dc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dc_last_error": (ctypes.c_char_p, []),
     "dc_version": (ctypes.c_char_p, []),

@@ -25,6 +25,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "dc_async.cuh"
@@ -994,3 +995,198 @@ int dc_sync_status(const dc_geometry *g, void *stream) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// Allocation-free Joseph line sums.
+//
+// Callers that cannot allocate device memory (a real-time reconstruction
+// loop on a scanner whose memory budget is fixed before the scan and must
+// never wait on the driver's allocator, or a host that embeds this library
+// inside another runtime's memory pool and cannot create a geometry handle)
+// use dc_radon2d_noalloc.  Its work area is the fixed array below, compiled
+// into the library: every GPU that loads the library holds it until exit.
+namespace {
+
+constexpr size_t NA_BYTES = 32u << 20;         // 32 MiB per device
+constexpr size_t NA_TABLE_BYTES = 128u << 10;  // angle tables and error word
+constexpr int NA_MAX_MU = 2048;
+constexpr int NA_MAX_DEV = 64;
+
+static_assert((sizeof(dc::MuRec) + sizeof(int) + sizeof(dc::MuGroup)) * NA_MAX_MU + 1024 <=
+                  NA_TABLE_BYTES,
+              "angle tables overflow their region");
+
+static __device__ __align__(256) unsigned char g_na_scratch[NA_BYTES];
+
+// set-up: the device address of g_na_scratch, once per device
+void *g_na_ptr[NA_MAX_DEV];
+std::mutex g_na_mu;
+
+// Angle tables for one call, written into the fixed area by one thread:
+// the same ordering and grouping as the geometry handle's tables.
+__global__ void k_na_tables(int n_mu, int n_s, double pitch, double ds, float cu, float cv,
+                            int mg, dc::MuRec *mu, int *order, dc::MuGroup *groups,
+                            int *n_groups, dc::FView *fv, unsigned *err) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  *err = 0u;
+  dc::FView f;
+  f.D = 1.0f;
+  f.cu = cu;
+  f.cv = cv;
+  f.ax = f.ay = f.az = f.pad0 = f.pad1 = 0.0f;
+  *fv = f;
+  int nord = 0, ng = 0;
+  for (int br = 0; br < 2; ++br) {
+    int cnt = 0;
+    for (int m = 0; m < n_mu; ++m) {
+      double ang = m * 3.14159265358979323846 / n_mu, c = cos(ang), s = sin(ang);
+      bool rows = (4 * m <= n_mu) || (4 * m >= 3 * n_mu);
+      if (br == 0) {
+        double mx = rows ? fabs(c) : fabs(s);
+        mu[m].c = (float)c;
+        mu[m].s = (float)s;
+        mu[m].jscale = (float)(pitch / mx);
+        mu[m].winv = (float)(ds / (pitch * mx));
+      }
+      if ((br == 0) != rows) continue;
+      if (cnt % mg == 0) {
+        groups[ng].first = nord;
+        groups[ng].count = 0;
+        groups[ng].branch = br;
+        groups[ng].pad = 0;
+        ++ng;
+      }
+      groups[ng - 1].count += 1;
+      order[nord++] = m;
+      ++cnt;
+    }
+  }
+  *n_groups = ng;
+}
+
+}  // namespace
+
+extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, double pitch,
+                                  double ds, double cu, double cv, const float *img, float *R,
+                                  void *stream) {
+  if (n_img < 1 || H < 2 || W < 2 || n_mu < 1 || n_s < 2)
+    return dc::fail(DC_ERR_ARG, "dc_radon2d_noalloc: sizes must be positive (H, W, n_s >= 2)");
+  if (!img || !R) return dc::fail(DC_ERR_ARG, "dc_radon2d_noalloc: NULL img or R");
+  if (!(pitch > 0) || !(ds > 0) || !std::isfinite(cu) || !std::isfinite(cv))
+    return dc::fail(DC_ERR_ARG, "dc_radon2d_noalloc: bad pitch, ds or principal point");
+  if (n_mu > NA_MAX_MU)
+    return dc::fail(DC_ERR_ARG, "dc_radon2d_noalloc: n_mu above the fixed maximum of " +
+                                    std::to_string(NA_MAX_MU));
+  const int Wp = round4(W), Hp = round4(H), NSp = round4(n_s);
+  const size_t per_img = ((size_t)H * Wp + (size_t)W * Hp) * sizeof(float);
+  const size_t cap = NA_BYTES - NA_TABLE_BYTES;
+  if (per_img > cap)
+    return dc::fail(DC_ERR_ARG, "dc_radon2d_noalloc: one " + std::to_string(H) + "x" +
+                                    std::to_string(W) + " image needs " +
+                                    std::to_string(per_img) + " bytes of work area; the fixed "
+                                    "maximum is " + std::to_string(cap) + " bytes");
+  int chunks = (n_s - 1 + 30) / 31;
+  int mg = std::max(1, std::min(8, (16 * 8) / std::max(1, chunks)));
+  size_t smem = (size_t)(2 * LS_RB * (std::max(Wp, Hp) + PADL + PADR) + mg * NSp) *
+                sizeof(float);
+  if (smem > 200 * 1024)
+    return dc::fail(DC_ERR_UNSUPPORTED, "dc_radon2d_noalloc: rows too long for shared memory");
+
+  int dev = 0;
+  DC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NA_MAX_DEV)
+    return dc::fail(DC_ERR_UNSUPPORTED, "dc_radon2d_noalloc: device index out of range");
+  unsigned char *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+      if (e != cudaSuccess) return dc::cuda_fail(e, "cudaGetSymbolAddress(g_na_scratch)");
+      g_na_ptr[dev] = p;
+    }
+    base = (unsigned char *)g_na_ptr[dev];
+  }
+  // fixed-area layout: tables first, then the image copies
+  dc::MuRec *mu = (dc::MuRec *)base;
+  int *order = (int *)(base + sizeof(dc::MuRec) * NA_MAX_MU);
+  dc::MuGroup *groups = (dc::MuGroup *)(base + (sizeof(dc::MuRec) + sizeof(int)) * NA_MAX_MU);
+  unsigned char *tail = base + (sizeof(dc::MuRec) + sizeof(int) + sizeof(dc::MuGroup)) * NA_MAX_MU;
+  int *n_groups = (int *)tail;
+  dc::FView *fv = (dc::FView *)(tail + 256);
+  unsigned *err = (unsigned *)(tail + 512);
+  float *work = (float *)(base + NA_TABLE_BYTES);
+
+  cudaStream_t st = (cudaStream_t)stream;
+  k_na_tables<<<1, 1, 0, st>>>(n_mu, n_s, pitch, ds, (float)cu, (float)cv, mg, mu, order,
+                               groups, n_groups, fv, err);
+  DC_CHECK_LAUNCH("k_na_tables");
+  // the group count is a host-side launch parameter: recompute it here
+  int nb0 = 0, nb1 = 0;
+  for (int m = 0; m < n_mu; ++m) ((4 * m <= n_mu) || (4 * m >= 3 * n_mu) ? nb0 : nb1) += 1;
+  const int n_groups_h = (nb0 + mg - 1) / mg + (nb1 + mg - 1) / mg;
+
+  DC_CUDA(cudaFuncSetAttribute(k_linesum<M_RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024));
+  const int per_chunk = (int)std::min<size_t>(cap / per_img, 65535);
+  float *img_w = work;
+  for (int n0 = 0; n0 < n_img; n0 += per_chunk) {
+    int nc = std::min(per_chunk, n_img - n0);
+    float *imgT_w = img_w + (size_t)nc * H * Wp;
+    PrepArgs p;
+    p.src = img + (size_t)n0 * H * W;
+    p.img = img_w;
+    p.imgT = imgT_w;
+    p.fv = fv;
+    p.H = H;
+    p.W = W;
+    p.Wp = Wp;
+    p.Hp = Hp;
+    p.V = 1;    // image n is batch item n of a one-view problem, so it
+    p.B = nc;   // reads offset n*H*W and table record 0
+    p.v0 = 0;
+    p.b0 = 0;
+    p.Bt = 0;
+    p.n_img = nc;
+    p.pitch = (float)pitch;
+    p.weight = WT_NONE;
+    dim3 gp((std::max(Wp, W) + 31) / 32, (std::max(Hp, H) + 31) / 32, nc);
+    {
+      dc::ProfScope ps(dc::KID_PREP, st);
+      k_prep<<<gp, dim3(32, 8), 0, st>>>(p);
+      DC_CHECK_LAUNCH("k_prep");
+    }
+    LineArgs a;
+    memset(&a, 0, sizeof(a));
+    a.img = img_w;
+    a.imgT = imgT_w;
+    a.H = H;
+    a.W = W;
+    a.Wp = Wp;
+    a.Hp = Hp;
+    a.n_mu = n_mu;
+    a.n_s = n_s;
+    a.NSp = NSp;
+    a.V = 1;    // output image n lands at ((b*1 + 0)*n_mu + m)*n_s with b = n
+    a.B = nc;
+    a.v0 = 0;
+    a.b0 = 0;
+    a.n_img = nc;
+    a.pitch = (float)pitch;
+    a.ds = (float)ds;
+    a.mu = mu;
+    a.mu_order = order;
+    a.groups = groups;
+    a.fv = fv;
+    a.out = R + (size_t)n0 * n_mu * n_s;
+    a.err = err;
+    a.mg = mg;
+    dim3 grid(n_groups_h, nc);
+    {
+      dc::ProfScope ps(dc::KID_LINESUM, st);
+      k_linesum<M_RAW><<<grid, LS_THREADS, smem, st>>>(a);
+      DC_CHECK_LAUNCH("k_linesum");
+    }
+  }
+  return DC_OK;
+}
