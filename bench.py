@@ -59,6 +59,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched-orbits measurement (for profiling)")
+    ap.add_argument("--train-only", action="store_true",
+                    help="only the training-step measurement (for profiling)")
     return ap.parse_args()
 
 
@@ -191,6 +197,113 @@ def run_reference(args, rank, world):
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- training
+def train_step_measure(args, dev, L, world):
+    """Forward + backward + AdamW step of the learnable redundancy weights:
+    sinusoidal orbit, 360 views, 256^2 detector, 256^3 volume, batch of 4
+    seeded phantoms, MSE against the phantom volumes, ReLU output."""
+    import torch
+    from paper_2410_14900_gb300 import api, synth
+    from paper_2410_14900_gb300.autograd import DefriseClackNet
+
+    w = synth.workload("sinusoid256_train")
+    geom = api.Geometry(w.desc_dict(), w.matrices(), w.orbit.vdl)
+    phs = w.phantoms()
+    g = torch.stack([synth.project_phantom(b, w.orbit, w.det_rows, w.det_cols, w.pitch,
+                                           device=dev, dtype=torch.float32) for b in phs])
+    tgt = torch.stack([synth.phantom_volume(b, w.vol_shape, w.voxel, device=dev) for b in phs])
+    net = DefriseClackNet(geom, init=0.5, relu=True, device=dev)
+    opt = torch.optim.AdamW(net.parameters(), lr=1e-3)
+
+    def step():
+        opt.zero_grad(set_to_none=True)
+        loss = torch.nn.functional.mse_loss(net(g), tgt)
+        loss.backward()
+        opt.step()
+        return loss
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    L.dc_profile_enable(1)
+    L.dc_profile_collect(None, None, 0)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        loss = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_k = np.zeros(16)
+    cnt_k = np.zeros(16, dtype=np.uint64)
+    nk = L.dc_profile_collect(ms_k.ctypes.data, cnt_k.ctypes.data, 16)
+    L.dc_profile_enable(0)
+    kernels = {L.dc_profile_kernel_name(i).decode(): round(float(ms_k[i]) / args.steps, 3)
+               for i in range(nk) if cnt_k[i]}
+    ms = e0.elapsed_time(e1) / args.steps
+    api.dc_sync_status(geom)
+    geom.close()
+    return {"workload": w.name, "ms_per_step": ms, "batch": w.batch,
+            "views": w.n_views, "volume": list(w.vol_shape), "weights": [w.n_views, w.n_mu, w.n_s],
+            "loss": float(loss.item()), "kernel_ms_per_step": kernels,
+            "optimizer": "AdamW (lr 1e-3)", "note": "forward + backward + optimizer step"}
+
+
+# --------------------------------------------------------------- batched
+def batched_measure(args, dev, L):
+    """12 uneven orbits (4 circular, 4 sinusoidal, 4 circle plus arc; 200-720
+    views; detectors 256^2 .. 616x480; volumes 128^3 .. 512^3) reconstructed by
+    one graph-captured batch run (per-problem filters, one persistent
+    backprojection), next to the same problems run one by one."""
+    import torch
+    from paper_2410_14900_gb300 import api, synth, tune
+
+    ws = synth.batch_workloads()
+    geoms = [api.Geometry(w.desc_dict(), w.matrices(), w.orbit.vdl) for w in ws]
+    g_list = [synth.project_phantom(w.phantoms()[0], w.orbit, w.det_rows, w.det_cols, w.pitch,
+                                    device=dev, dtype=torch.float32).contiguous() for w in ws]
+    vols = [torch.empty(gm.vol_shape, device=dev) for gm in geoms]
+    updates = float(sum(w.n_views * np.prod(w.vol_shape) for w in ws))
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"problems": len(ws), "views": [w.n_views for w in ws],
+           "detectors": [[w.det_rows, w.det_cols] for w in ws],
+           "volumes": [w.vol_shape[0] for w in ws], "voxel_view_updates": updates}
+    for dtype in ("f32", "bf16"):
+        batch = api.Batch(geoms, dtype=dtype, kahan=(dtype != "f32"))
+        tuned = tune.autotune_batch(batch, g_list, vols)
+        batch.capture(g_list, vols)
+        ms = timed(batch.replay, args.steps)
+        out[f"{dtype}_graph_ms_per_batch"] = ms
+        out[f"{dtype}_bp_nz"] = tuned["bp_nz"]
+        batch.close()
+        del batch
+    def seq():
+        for gm, g, v in zip(geoms, g_list, vols):
+            gF, _ = api.dc_filter(gm, g[None])
+            api.dc_backproject(gm, gF, out=v[None])
+    out["f32_sequential_ms_per_batch"] = timed(seq, args.steps)
+    out["f32_graph_ms_per_volume"] = out["f32_graph_ms_per_batch"] / len(ws)
+    for gm in geoms:
+        api.dc_sync_status(gm)
+        gm.close()
+    return out
 
 
 # --------------------------------------------------------------- our arm
@@ -352,6 +465,16 @@ def run_ours(args, rank, world, local_rank):
             forms[f"{st}_storage_kahan_ms_per_volume"] = f0.elapsed_time(f1) / args.steps
             del gF2
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_measure(args, dev, L)
+
+    train = None
+    if not args.no_train:
+        del gF, vol
+        torch.cuda.empty_cache()
+        train = train_step_measure(args, dev, L, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g_np = g[0].double().cpu().numpy()
@@ -371,7 +494,8 @@ def run_ours(args, rank, world, local_rank):
                            "voxel_mm": list(w.voxel), "storage": args.storage,
                            "batch_per_gpu": B, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (g 390 MB, f 537 MB), no flush"},
-                "roofline": roof, "breakdown": breakdown, "forms": forms,
+                "roofline": roof, "breakdown": breakdown, "forms": forms, "train_step": train,
+                "batched": batched,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(n_launch),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
@@ -385,6 +509,20 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.batched_only:
+        import torch
+        from paper_2410_14900_gb300 import _lib
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"batched": batched_measure(args, torch.device("cuda", local_rank),
+                                                     _lib.load())}), flush=True)
+        return
+    if args.train_only:
+        import torch
+        from paper_2410_14900_gb300 import _lib
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"train_step": train_step_measure(args, torch.device("cuda", local_rank),
+                                                           _lib.load(), world)}), flush=True)
         return
     if world > 1:
         import torch

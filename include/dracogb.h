@@ -185,6 +185,44 @@ int dc_backproject_adjoint(const dc_geometry *geom, int B, const float *grad_vol
                            const float *relu_vol, float *grad_gF, void *stream);
 
 /*
+ * Batched reconstruction of several problems (orbits with uneven view
+ * counts, detectors and volumes): Eq. 12 for each, with the backprojection
+ * of all problems done by one persistent kernel that takes (problem, voxel
+ * box) items from a device counter, largest view count first.
+ *
+ * dc_batch_create -- plans a batch of n <= 32 geometries (not owned; they
+ *   must outlive the batch) for g^F storage `dtype` and flags DC_KAHAN |
+ *   DC_RELU.  Allocates the batch's filtered projections and tables.  Every
+ *   detector row must be a multiple of 16 bytes in `dtype` (tiled TMA loads).
+ * dc_batch_run -- g[i]: device [V_i][H_i][W_i] FP32; W[i]: device
+ *   [V_i][n_mu_i][n_s_i] or NULL entries (W itself may be NULL: all 1/2);
+ *   vol[i]: device [Z_i][Y_i][X_i] FP32, overwritten.  Allocates nothing, so
+ *   a run can be captured in a CUDA graph and replayed with the same
+ *   pointers.  Uses each geometry's work area: one run at a time per batch.
+ * dc_batch_set_bp_nz -- voxels per thread along z in the backprojection
+ *   (16 or 32), for the autotuner.
+ */
+typedef struct dc_batch dc_batch;
+int dc_batch_create(int n, dc_geometry *const *geoms, int dtype, unsigned flags,
+                    dc_batch **out);
+int dc_batch_run(dc_batch *batch, const float *const *g, const float *const *W,
+                 float *const *vol, void *stream);
+int dc_batch_set_bp_nz(dc_batch *batch, int nz);
+void dc_batch_destroy(dc_batch *batch);
+
+/*
+ * Tuning knobs of a geometry handle (chosen by the autotuner):
+ * chunk_images -- images (view x batch item) the filter processes together,
+ *   1 <= chunk_images <= the capacity its work area was sized for;
+ * bp_nz -- voxels per thread along z in the backprojection (16 or 32).
+ * 0 keeps a value.  dc_geometry_get_tuning reads them (any pointer may be
+ * NULL).
+ */
+int dc_geometry_set_tuning(dc_geometry *geom, int chunk_images, int bp_nz);
+int dc_geometry_get_tuning(const dc_geometry *geom, int *chunk_images, int *chunk_capacity,
+                           int *bp_nz);
+
+/*
  * Per-step entry points (the layers of Fig. 2), for testing and for callers
  * that compose the network themselves.
  *
@@ -225,7 +263,7 @@ int dc_sync_status(const dc_geometry *geom, void *stream);
  *   cu, cv: principal point (column, row) shared by all images; pitch, ds,
  *           mu_m = m pi / n_mu and s_k as for a geometry handle.
  * Limits: n_mu <= 2048; one image needs (H * round4(W) + W * round4(H)) * 4
- * bytes of the fixed area, at most 32 MiB - 128 KiB (larger requests return
+ * bytes of the fixed area, at most 32 MiB - 256 KiB (larger requests return
  * DC_ERR_ARG with the numbers); images are processed in groups that fit.
  * The first call on a device looks up the array's device address (set-up);
  * make that first call before any stream capture.  All calls share the array

@@ -52,6 +52,13 @@ _SIGS = {
     "dc_radon2d": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "dc_radon2d_adjoint": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "dc_sync_status": (ctypes.c_int, [_P, _P]),
+    "dc_batch_create": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int, ctypes.c_uint,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "dc_batch_run": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "dc_batch_set_bp_nz": (ctypes.c_int, [_P, ctypes.c_int]),
+    "dc_batch_destroy": (None, [_P]),
+    "dc_geometry_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "dc_geometry_get_tuning": (ctypes.c_int, [_P, _P, _P, _P]),
     "dc_radon2d_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, _P, _P, _P]),

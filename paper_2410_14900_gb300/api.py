@@ -236,6 +236,79 @@ def dc_sync_status(geom: Geometry):
     check(_lib.load().dc_sync_status(geom.handle, _stream()), "dc_sync_status")
 
 
+def dc_geometry_set_tuning(geom: Geometry, chunk_images: int = 0, bp_nz: int = 0):
+    check(_lib.load().dc_geometry_set_tuning(geom.handle, int(chunk_images), int(bp_nz)),
+          "dc_geometry_set_tuning")
+
+
+def dc_geometry_get_tuning(geom: Geometry) -> dict:
+    a, c, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(_lib.load().dc_geometry_get_tuning(geom.handle, ctypes.byref(a), ctypes.byref(c),
+                                             ctypes.byref(z)), "dc_geometry_get_tuning")
+    return {"chunk_images": a.value, "chunk_capacity": c.value, "bp_nz": z.value}
+
+
+class Batch:
+    """A batch of reconstruction problems (dc_batch_create / dc_batch_run).
+
+    run() filters every problem and backprojects all of them with one
+    persistent kernel; it allocates nothing, so it can be captured in a CUDA
+    graph (capture()) and replayed (replay()).
+    """
+
+    def __init__(self, geoms, dtype: str = "f32", kahan: bool = False, relu: bool = False):
+        L = _lib.load()
+        self.geoms = list(geoms)
+        arr = (ctypes.c_void_p * len(self.geoms))(*[g.handle for g in self.geoms])
+        flags = (DC_KAHAN if kahan else 0) | (DC_RELU if relu else 0)
+        h = ctypes.c_void_p()
+        check(L.dc_batch_create(len(self.geoms), arr, _DTYPES[dtype][0], flags, ctypes.byref(h)),
+              "dc_batch_create")
+        self._h = h
+        self._lib = L
+        self.graph = None
+
+    def set_bp_nz(self, nz: int):
+        check(self._lib.dc_batch_set_bp_nz(self._h, int(nz)), "dc_batch_set_bp_nz")
+
+    def run(self, g_list, vol_list, W_list=None):
+        n = len(self.geoms)
+        for i, (geom, g, v) in enumerate(zip(self.geoms, g_list, vol_list)):
+            _need(g, f"g[{i}]", torch.float32, (geom.V, geom.H, geom.W))
+            _need(v, f"vol[{i}]", torch.float32, geom.vol_shape)
+        gp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in g_list])
+        vp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in vol_list])
+        wp = None
+        if W_list is not None:
+            wp = (ctypes.c_void_p * n)(*[0 if t is None else t.data_ptr() for t in W_list])
+        check(self._lib.dc_batch_run(self._h, gp, wp, vp, _stream()), "dc_batch_run")
+
+    def capture(self, g_list, vol_list, W_list=None):
+        """Record one run into a CUDA graph (after one eager run, which sets
+        the kernels' shared-memory attributes outside the capture)."""
+        self.run(g_list, vol_list, W_list)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run(g_list, vol_list, W_list)
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self.graph = None
+            self._lib.dc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def reconstruct(geom: Geometry, g: torch.Tensor, W: Optional[torch.Tensor] = None,
                 dtype: str = "f32", kahan: bool = False, relu: bool = False) -> torch.Tensor:
     """Eq. 12: f = A3d^T w_d A2d^T D w_red w_sino D A2d w_cos g."""

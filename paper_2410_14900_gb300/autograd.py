@@ -1,0 +1,82 @@
+"""Differentiable Defrise-Clack reconstruction (Ye et al., DRACO, Sec. 2.3).
+
+The network of Eq. 12 with the redundancy weight (Eq. 10) as its only
+trainable layer:
+
+    f = ReLU(A3d^T w_d A2d^T D_b (W K) w_sino D_f A2d w_cos g)
+
+forward  -> dc_filter, dc_backproject (optional ReLU)
+backward -> dc_backproject_adjoint (masked by the ReLU), dc_filter_adjoint
+
+Nothing but g, W and (with ReLU) the output volume is kept between the
+passes: the filter adjoint recomputes Grangeat's function S view-chunk by
+view-chunk, so training memory is two projection sets and the volumes.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+import torch
+
+from . import api
+
+
+class DefriseClackFunction(torch.autograd.Function):
+    """f = A3d^T filter(g, W) with gradients for g and W."""
+
+    @staticmethod
+    def forward(ctx, g: torch.Tensor, W: Optional[torch.Tensor], geom: api.Geometry,
+                relu: bool = False, view_chunk: int = 0):
+        g = g.contiguous()
+        Wc = None if W is None else W.contiguous()
+        gF, _ = api.dc_filter(geom, g, Wc)
+        vol = api.dc_backproject(geom, gF, relu=relu)
+        del gF
+        ctx.geom = geom
+        ctx.relu = relu
+        ctx.view_chunk = view_chunk
+        ctx.has_W = W is not None
+        ctx.save_for_backward(g, Wc if Wc is not None else g.new_empty(0),
+                              vol if relu else g.new_empty(0))
+        return vol
+
+    @staticmethod
+    def backward(ctx, grad_vol: torch.Tensor):
+        g, W, vol = ctx.saved_tensors
+        W = W if ctx.has_W else None
+        relu_vol = vol if ctx.relu else None
+        need_g, need_W = ctx.needs_input_grad[0], ctx.needs_input_grad[1] and ctx.has_W
+        if not (need_g or need_W):
+            return None, None, None, None, None
+        grad_gF = api.dc_backproject_adjoint(ctx.geom, grad_vol.contiguous(), relu_vol)
+        gg, gW = api.dc_filter_adjoint(ctx.geom, grad_gF, g, W, want_grad_g=need_g,
+                                       want_grad_W=need_W, view_chunk=ctx.view_chunk)
+        return gg, gW, None, None, None
+
+
+def reconstruct(g: torch.Tensor, W: Optional[torch.Tensor], geom: api.Geometry,
+                relu: bool = False, view_chunk: int = 0) -> torch.Tensor:
+    """Differentiable Eq. 12 (see DefriseClackFunction)."""
+    return DefriseClackFunction.apply(g, W, geom, relu, view_chunk)
+
+
+class DefriseClackNet(torch.nn.Module):
+    """The reconstruction network with a learnable redundancy weight W.
+
+    W has shape [V, n_mu, n_s] (entry k on the half grid s_{k+1/2}) and is
+    multiplied by K = -(1/4pi^2)|v.theta|/sqrt(s^2+D^2) inside the library,
+    so W = 1/2 is the exact full-circle value (Eq. 14).
+    """
+
+    def __init__(self, geom: api.Geometry, init: float = 0.5, relu: bool = True,
+                 view_chunk: int = 0, device=None):
+        super().__init__()
+        self.geom = geom
+        self.relu = relu
+        self.view_chunk = view_chunk
+        shape = (geom.V,) + geom.sino_shape
+        self.W = torch.nn.Parameter(torch.full(shape, float(init), device=device,
+                                               dtype=torch.float32))
+
+    def forward(self, g: torch.Tensor) -> torch.Tensor:
+        return reconstruct(g, self.W, self.geom, self.relu, self.view_chunk)

@@ -15,8 +15,10 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "dc_async.cuh"
 #include "dc_common.cuh"
@@ -248,45 +250,53 @@ __device__ __forceinline__ float sld<__nv_bfloat16>(const __nv_bfloat16 *p) {
 template <>
 __device__ __forceinline__ float sld<__half>(const __half *p) { return __half2float(*p); }
 
-template <typename T, bool KAHAN>
-__global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_tma(BPArgs a, unsigned *err,
-                                                          const __grid_constant__ CUtensorMap tmn,
-                                                          const __grid_constant__ CUtensorMap tmw) {
-  __shared__ __align__(128) unsigned char sbuf[TB_NS][TB_BH * TB_BWW * sizeof(T)];
-  __shared__ uint64_t full[TB_NS];
-  __shared__ dc::BPView sv[TB_VCH];
-  __shared__ int4 vtab[TB_VCH];
+// Shared memory of k_bp3d_tma (dynamic): NS raw TMA stages, then two FP32
+// work tiles of interleaved tap pairs (g[r][j], g[r][j+1]) with a row stride
+// of TB_S2 float2 (8 mod 16): adjacent rows put one column on different
+// banks, and a bilinear row pair is one 64-bit load.
+constexpr int TB_S2 = TB_BWW + 8;
+template <typename T>
+constexpr size_t bp_tma_smem() {
+  return (size_t)TB_NS * TB_BH * TB_BWW * sizeof(T) + 2 * (size_t)TB_BH * TB_S2 * sizeof(float2);
+}
+
+// One CTA backprojects one box of 16 x 16 x NZ voxels (box indices bxi, byi
+// and bzi = batch item * z-blocks + z-block) over every view.  `it` is the
+// CTA's running view counter (mbarrier stage and parity), carried across
+// boxes by the persistent kernel.  Returns false if a bounded wait gave up.
+template <typename T, bool KAHAN, int NZ>
+__device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtensorMap *tmn,
+                                       const CUtensorMap *tmw, unsigned *err, int bxi, int byi,
+                                       int bzi, unsigned char *dsm, uint64_t *full,
+                                       dc::BPView *sv, int4 *vtab, unsigned &it) {
+  constexpr size_t STAGE_BYTES = (size_t)TB_BH * TB_BWW * sizeof(T);
+  float2 *wtile0 = (float2 *)(dsm + TB_NS * STAGE_BYTES);
 
   const int tid = threadIdx.y * TB_TX + threadIdx.x;
-  const int ix = blockIdx.x * TB_TX + threadIdx.x;
-  const int iy = blockIdx.y * TB_TY + threadIdx.y;
-  const int zblocks = (a.nz + TB_NZ - 1) / TB_NZ;
-  const int b = blockIdx.z / zblocks;
-  const int z0 = (blockIdx.z % zblocks) * TB_NZ;
+  const int ix = bxi * TB_TX + threadIdx.x;
+  const int iy = byi * TB_TY + threadIdx.y;
+  const int zblocks = (a.nz + NZ - 1) / NZ;
+  const int b = bzi / zblocks;
+  const int z0 = (bzi % zblocks) * NZ;
   const float cx = 0.5f * (float)(a.nx - 1), cy = 0.5f * (float)(a.ny - 1),
               cz = 0.5f * (float)(a.nz - 1);
   const float xo = ((float)ix - cx) * a.dx;
   const float yo = ((float)iy - cy) * a.dy;
   const float zo = ((float)z0 - cz) * a.dz;
   // extremal voxel centres of this CTA's box (clipped to the volume)
-  const float bx0 = ((float)(blockIdx.x * TB_TX) - cx) * a.dx;
-  const float bx1 = ((float)min(blockIdx.x * TB_TX + TB_TX - 1, a.nx - 1) - cx) * a.dx;
-  const float by0 = ((float)(blockIdx.y * TB_TY) - cy) * a.dy;
-  const float by1 = ((float)min(blockIdx.y * TB_TY + TB_TY - 1, a.ny - 1) - cy) * a.dy;
+  const float bx0 = ((float)(bxi * TB_TX) - cx) * a.dx;
+  const float bx1 = ((float)min(bxi * TB_TX + TB_TX - 1, a.nx - 1) - cx) * a.dx;
+  const float by0 = ((float)(byi * TB_TY) - cy) * a.dy;
+  const float by1 = ((float)min(byi * TB_TY + TB_TY - 1, a.ny - 1) - cy) * a.dy;
   const float bz0 = zo;
-  const float bz1 = ((float)min(z0 + TB_NZ - 1, a.nz - 1) - cz) * a.dz;
+  const float bz1 = ((float)min(z0 + NZ - 1, a.nz - 1) - cz) * a.dz;
   const size_t np = (size_t)a.H * a.W;
   const T *gbase = (const T *)a.gF + (size_t)b * a.V * np;
 
-  if (tid == 0) {
-    for (int q = 0; q < TB_NS; ++q) dc::mbar_init(&full[q], 1);
-    dc::fence_barrier_init();
-  }
-  float acc[TB_NZ], cmp[TB_NZ];
+  float acc[NZ], cmp[NZ];
 #pragma unroll
-  for (int k = 0; k < TB_NZ; ++k) acc[k] = cmp[k] = 0.0f;
+  for (int k = 0; k < NZ; ++k) acc[k] = cmp[k] = 0.0f;
 
-  unsigned it = 0;  // running view counter: stage it % NS, parity (it / NS) & 1
   bool ok = true;
   for (int c0 = 0; c0 < a.V && ok; c0 += TB_VCH) {
     const int nvc = min(TB_VCH, a.V - c0);
@@ -338,13 +348,14 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_tma(BPArgs a, unsigned
     __syncthreads();
     auto issue = [&](int vi, unsigned s) {
       const int4 t = vtab[vi];
+      unsigned char *dst = dsm + s * STAGE_BYTES;
       dc::fence_proxy_async();
       if (t.z == FP_NARROW) {
         dc::mbar_arrive_expect_tx(&full[s], TB_BWN * TB_BH * sizeof(T));
-        dc::tma_load_3d(sbuf[s], &tmn, t.x, t.y, b * a.V + c0 + vi, &full[s]);
+        dc::tma_load_3d(dst, tmn, t.x, t.y, b * a.V + c0 + vi, &full[s]);
       } else if (t.z == FP_WIDE) {
         dc::mbar_arrive_expect_tx(&full[s], TB_BWW * TB_BH * sizeof(T));
-        dc::tma_load_3d(sbuf[s], &tmw, t.x, t.y, b * a.V + c0 + vi, &full[s]);
+        dc::tma_load_3d(dst, tmw, t.x, t.y, b * a.V + c0 + vi, &full[s]);
       } else {
         dc::mbar_arrive(&full[s]);
       }
@@ -355,42 +366,54 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_tma(BPArgs a, unsigned
     for (int vi = 0; vi < nvc; ++vi, ++it) {
       const unsigned s = it % TB_NS;
       const int4 t = vtab[vi];
+      const int i = c0 + vi;
+      float sc = 1.0f;
+      if (a.scale) sc = a.scale[(size_t)b * a.V + i];
       bool w_ok = dc::mbar_wait_bounded(&full[s], (it / TB_NS) & 1, err);
+      float2 *wt = wtile0 + (size_t)(it & 1) * TB_BH * TB_S2;
+      const bool staged = (t.z == FP_NARROW || t.z == FP_WIDE);
+      if (w_ok && staged) {
+        // raw box -> FP32 pair tile (times the FP16 scale)
+        const T *raw = (const T *)(dsm + s * STAGE_BYTES);
+        const int bw = t.w;
+        for (int e = tid; e < TB_BH * bw; e += TB_TX * TB_TY) {
+          int r = e / bw, j = e - r * bw;
+          float g0 = sld(raw + e) * sc;
+          float g1 = (j + 1 < bw) ? sld(raw + e + 1) * sc : 0.0f;
+          wt[r * TB_S2 + j] = make_float2(g0, g1);
+        }
+      }
       if (__syncthreads_or(!w_ok)) {
         ok = false;
         break;
       }
+      if (tid == 0 && vi + TB_NS - 1 < nvc) issue(vi + TB_NS - 1, (it + TB_NS - 1) % TB_NS);
       const dc::BPView w = sv[vi];
-      const int i = c0 + vi;
-      float sc = 1.0f;
-      if (a.scale) sc = a.scale[(size_t)b * a.V + i];
       float U0 = fmaf(w.r0.x, xo, fmaf(w.r0.y, yo, fmaf(w.r0.z, zo, w.r0.w)));
       float V0 = fmaf(w.r1.x, xo, fmaf(w.r1.y, yo, fmaf(w.r1.z, zo, w.r1.w)));
       float W0 = fmaf(w.r2.x, xo, fmaf(w.r2.y, yo, fmaf(w.r2.z, zo, w.r2.w)));
       float dU = w.r0.z * a.dz, dV = w.r1.z * a.dz, dW = w.r2.z * a.dz;
       float ex = w.ca.x + xo, ey = w.ca.y + yo, ez0 = w.ca.z + zo;
       float rho2 = fmaf(ex, ex, ey * ey);
-      if (t.z == FP_NARROW || t.z == FP_WIDE) {
-        const T *tile = (const T *)sbuf[s];
-        const int stride = t.w;
+      if (staged) {
         const float cul = w.pp.x - (float)t.x, cvl = w.pp.y - (float)t.y;
-        const float umx = (float)stride - 1.001f, vmx = (float)TB_BH - 1.001f;
+        const float umx = (float)t.w - 1.001f, vmx = (float)TB_BH - 1.001f;
         if (w.ca.w != 0.0f) {
           // circle view: u and the depth do not change along the column
           float rw = dc::rcp_approx(W0);
           float u = fminf(fmaxf(fmaf(U0, rw, cul), 0.0f), umx), fu;
           int j = dc::floor_frac(u, fu);
-          const T *col = tile + j;
+          const float2 *col = wt + j;
           float vb = fmaf(V0, rw, cvl), dv = dV * rw;
 #pragma unroll
-          for (int k = 0; k < TB_NZ; ++k) {
+          for (int k = 0; k < NZ; ++k) {
             float kf = (float)k;
             float v = fminf(fmaxf(fmaf(kf, dv, vb), 0.0f), vmx), fv;
             int r = dc::floor_frac(v, fv);
-            const T *p = col + r * stride;
-            float g00 = sld(p), g01 = sld(p + 1), g10 = sld(p + stride), g11 = sld(p + stride + 1);
-            float x0 = fmaf(fu, g01 - g00, g00), x1 = fmaf(fu, g11 - g10, g10);
-            float val = fmaf(fv, x1 - x0, x0) * sc;
+            const float2 *p = col + r * TB_S2;
+            float2 q0 = p[0], q1 = p[TB_S2];
+            float x0 = fmaf(fu, q0.y - q0.x, q0.x), x1 = fmaf(fu, q1.y - q1.x, q1.x);
+            float val = fmaf(fv, x1 - x0, x0);
             float ez = fmaf(kf, a.dz, ez0);
             float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
             if (KAHAN) {
@@ -404,17 +427,17 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_tma(BPArgs a, unsigned
           }
         } else {
 #pragma unroll
-          for (int k = 0; k < TB_NZ; ++k) {
+          for (int k = 0; k < NZ; ++k) {
             float kf = (float)k;
             float rw = dc::rcp_approx(fmaf(kf, dW, W0));
             float u = fminf(fmaxf(fmaf(fmaf(kf, dU, U0), rw, cul), 0.0f), umx);
             float v = fminf(fmaxf(fmaf(fmaf(kf, dV, V0), rw, cvl), 0.0f), vmx);
             float fu, fv;
             int j = dc::floor_frac(u, fu), r = dc::floor_frac(v, fv);
-            const T *p = tile + r * stride + j;
-            float g00 = sld(p), g01 = sld(p + 1), g10 = sld(p + stride), g11 = sld(p + stride + 1);
-            float x0 = fmaf(fu, g01 - g00, g00), x1 = fmaf(fu, g11 - g10, g10);
-            float val = fmaf(fv, x1 - x0, x0) * sc;
+            const float2 *p = wt + r * TB_S2 + j;
+            float2 q0 = p[0], q1 = p[TB_S2];
+            float x0 = fmaf(fu, q0.y - q0.x, q0.x), x1 = fmaf(fu, q1.y - q1.x, q1.x);
+            float val = fmaf(fv, x1 - x0, x0);
             float ez = fmaf(kf, a.dz, ez0);
             float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
             if (KAHAN) {
@@ -430,7 +453,7 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_tma(BPArgs a, unsigned
       } else if (t.z == FP_GLOBAL) {
         const T *img = gbase + (size_t)i * np;
 #pragma unroll
-        for (int k = 0; k < TB_NZ; ++k) {
+        for (int k = 0; k < NZ; ++k) {
           float kf = (float)k;
           float dep = fmaf(kf, dW, W0);
           if (!(dep > 0.0f)) continue;
@@ -450,25 +473,294 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_tma(BPArgs a, unsigned
           }
         }
       }
-      __syncthreads();
-      if (tid == 0 && vi + TB_NS - 1 < nvc) issue(vi + TB_NS - 1, (it + TB_NS - 1) % TB_NS);
     }
   }
-  if (!ok) {
-    for (int q = 0; q < TB_NS; ++q) dc::mbar_wait_bounded(&full[q], 0, nullptr);
-    return;
-  }
-  if (ix >= a.nx || iy >= a.ny) return;
+  if (!ok) return false;
+  if (ix >= a.nx || iy >= a.ny) return true;
   const size_t nvox = (size_t)a.nx * a.ny * a.nz;
 #pragma unroll
-  for (int k = 0; k < TB_NZ; ++k) {
+  for (int k = 0; k < NZ; ++k) {
     int iz = z0 + k;
     if (iz >= a.nz) break;
     size_t o = (size_t)b * nvox + ((size_t)iz * a.ny + iy) * a.nx + ix;
     float f = acc[k];
-    if (a.flags & DC_ACCUM) f += a.vol[o];
+    if (a.flags & DC_ACCUM) f += vol[o];
     if ((a.flags & DC_RELU) && f < 0.0f) f = 0.0f;
-    a.vol[o] = f;
+    vol[o] = f;
+  }
+  return true;
+}
+
+template <typename T, bool KAHAN, int NZ>
+__global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_tma(BPArgs a, unsigned *err,
+                                                             const __grid_constant__ CUtensorMap tmn,
+                                                             const __grid_constant__ CUtensorMap tmw) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ uint64_t full[TB_NS];
+  __shared__ dc::BPView sv[TB_VCH];
+  __shared__ int4 vtab[TB_VCH];
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    for (int q = 0; q < TB_NS; ++q) dc::mbar_init(&full[q], 1);
+    dc::fence_barrier_init();
+  }
+  __syncthreads();
+  unsigned it = 0;
+  if (!bp_box<T, KAHAN, NZ>(a, a.vol, &tmn, &tmw, err, blockIdx.x, blockIdx.y, blockIdx.z, dsm,
+                            full, sv, vtab, it)) {
+    for (int q = 0; q < TB_NS; ++q) dc::mbar_wait_bounded(&full[q], 0, nullptr);
+  }
+}
+
+// Persistent backprojection of a batch of problems (orbits of uneven view
+// counts, detectors and volumes): CTAs take (problem, box) items from a
+// device counter until all are done.  Items are ordered by problem, largest
+// view count first, so the long boxes start early.
+constexpr int DC_MAX_BATCH = 32;
+struct BatchProblem {
+  BPArgs a;               // a.vol is unused: the output comes with the run
+  const CUtensorMap *tmn; // global-memory tensor maps over the problem's g^F
+  const CUtensorMap *tmw;
+  int bx, by, bz;         // boxes per dimension (bz includes the batch)
+  long long first;        // first work item of this problem
+};
+struct BatchRun {
+  float *vol[DC_MAX_BATCH];
+};
+
+template <typename T, bool KAHAN, int NZ>
+__global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_batched(const BatchProblem *probs,
+                                                                 int nprob, long long total,
+                                                                 unsigned long long *counter,
+                                                                 unsigned *err, BatchRun run) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ uint64_t full[TB_NS];
+  __shared__ dc::BPView sv[TB_VCH];
+  __shared__ int4 vtab[TB_VCH];
+  __shared__ long long item;
+  const int tid = threadIdx.y * TB_TX + threadIdx.x;
+  if (tid == 0) {
+    for (int q = 0; q < TB_NS; ++q) dc::mbar_init(&full[q], 1);
+    dc::fence_barrier_init();
+  }
+  unsigned it = 0;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) item = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const long long w = item;
+    if (w >= total) break;
+    int p = 0;
+    while (p + 1 < nprob && probs[p + 1].first <= w) ++p;
+    const BatchProblem &P = probs[p];
+    long long lw = w - P.first;
+    int bxi = (int)(lw % P.bx);
+    long long rest = lw / P.bx;
+    int byi = (int)(rest % P.by);
+    int bzi = (int)(rest / P.by);
+    if (!bp_box<T, KAHAN, NZ>(P.a, run.vol[p], P.tmn, P.tmw, err, bxi, byi, bzi, dsm, full, sv,
+                              vtab, it)) {
+      for (int q = 0; q < TB_NS; ++q) dc::mbar_wait_bounded(&full[q], 0, nullptr);
+      return;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// Transpose of the staged backprojection.  Same CTA boxes and footprints as
+// the forward kernel; for every view the CTA's voxels scatter their weighted
+// gradients into a shared-memory footprint tile (row stride 65, so one
+// column of adjacent rows sits on different banks), which is then added to
+// g^F's gradient with one global atomic per non-zero pixel.
+//
+// The tile accumulates in 32-bit fixed point, because integer shared-memory
+// atomics are native while floating-point ones are not.  The unit is chosen
+// per (box, view) from a rigorous bound on any pixel sum: every voxel's four
+// bilinear weights sum to one, so a pixel gets at most the box's total,
+// nvox * max|g| / d_min^2, with d_min the source's distance to the box
+// (centre distance minus half-diagonal); tighter and still rigorous is
+// sum_box |g| / d_min^2, since every voxel's weights sum to one and each
+// voxel's distance is at least d_min.  That bound maps to 2^30, so the sums
+// cannot overflow; each contribution is rounded to the nearest unit.
+constexpr int TA_S = TB_BWW + 1;
+static_assert(TB_BWW == 64, "the tile flush indexes columns with a 6-bit shift");
+
+__global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) {
+  __shared__ int tile[TB_BH * TA_S];
+  __shared__ dc::BPView sv[TB_VCH];
+  __shared__ int4 vtab[TB_VCH];
+  __shared__ float wsum[TB_TX * TB_TY / 32];
+  const int tid = threadIdx.y * TB_TX + threadIdx.x;
+  const int ix = blockIdx.x * TB_TX + threadIdx.x;
+  const int iy = blockIdx.y * TB_TY + threadIdx.y;
+  const int zblocks = (a.nz + TB_NZ - 1) / TB_NZ;
+  const int b = blockIdx.z / zblocks;
+  const int z0 = (blockIdx.z % zblocks) * TB_NZ;
+  const float cx = 0.5f * (float)(a.nx - 1), cy = 0.5f * (float)(a.ny - 1),
+              cz = 0.5f * (float)(a.nz - 1);
+  const float xo = ((float)ix - cx) * a.dx;
+  const float yo = ((float)iy - cy) * a.dy;
+  const float zo = ((float)z0 - cz) * a.dz;
+  const float bx0 = ((float)(blockIdx.x * TB_TX) - cx) * a.dx;
+  const float bx1 = ((float)min(blockIdx.x * TB_TX + TB_TX - 1, a.nx - 1) - cx) * a.dx;
+  const float by0 = ((float)(blockIdx.y * TB_TY) - cy) * a.dy;
+  const float by1 = ((float)min(blockIdx.y * TB_TY + TB_TY - 1, a.ny - 1) - cy) * a.dy;
+  const float bz0 = zo;
+  const float bz1 = ((float)min(z0 + TB_NZ - 1, a.nz - 1) - cz) * a.dz;
+  // box centre and half-diagonal (for the distance bound)
+  const float bcx = 0.5f * (bx0 + bx1), bcy = 0.5f * (by0 + by1), bcz = 0.5f * (bz0 + bz1);
+  const float bhd = 0.5f * sqrtf((bx1 - bx0) * (bx1 - bx0) + (by1 - by0) * (by1 - by0) +
+                                 (bz1 - bz0) * (bz1 - bz0)) + 0.5f * (a.dx + a.dy + a.dz);
+  const size_t np = (size_t)a.H * a.W;
+  const size_t nvox = (size_t)a.nx * a.ny * a.nz;
+  const bool inside = (ix < a.nx && iy < a.ny);
+  float gv[TB_NZ];
+  float gs = 0.0f;
+#pragma unroll
+  for (int k = 0; k < TB_NZ; ++k) {
+    int iz = z0 + k;
+    gv[k] = 0.0f;
+    if (inside && iz < a.nz) {
+      size_t o = (size_t)b * nvox + ((size_t)iz * a.ny + iy) * a.nx + ix;
+      float g = a.grad_vol[o];
+      if (a.relu_vol && !(a.relu_vol[o] > 0.0f)) g = 0.0f;
+      gv[k] = g;
+      gs += fabsf(g);
+    }
+  }
+  const bool any = gs > 0.0f;
+  for (int o = 16; o > 0; o >>= 1) gs += __shfl_xor_sync(0xffffffffu, gs, o);
+  if ((tid & 31) == 0) wsum[tid >> 5] = gs;
+  for (int e = tid; e < TB_BH * TA_S; e += TB_TX * TB_TY) tile[e] = 0;
+  __syncthreads();
+  float gsum = 0.0f;
+  for (int q = 0; q < TB_TX * TB_TY / 32; ++q) gsum += wsum[q];
+  gsum *= 1.0001f;  // headroom for the rounding of this sum
+  if (!(gsum > 0.0f)) return;  // nothing to scatter from this box (CTA-uniform)
+  float *gbase = a.grad_gF + (size_t)b * a.V * np;
+
+  for (int c0 = 0; c0 < a.V; c0 += TB_VCH) {
+    const int nvc = min(TB_VCH, a.V - c0);
+    __syncthreads();
+    {  // footprints: thread = (view, corner), as in the forward kernel
+      const int vi = tid >> 3, cr = tid & 7;
+      float umin = 0.0f, umax = 0.0f, vmin = 0.0f, vmax = 0.0f;
+      int good = 1;
+      if (vi < nvc) {
+        const dc::BPView w = a.views[c0 + vi];
+        if (cr == 0) sv[vi] = w;
+        float X = (cr & 1) ? bx1 : bx0, Y = (cr & 2) ? by1 : by0, Z = (cr & 4) ? bz1 : bz0;
+        float U = fmaf(w.r0.x, X, fmaf(w.r0.y, Y, fmaf(w.r0.z, Z, w.r0.w)));
+        float Vv = fmaf(w.r1.x, X, fmaf(w.r1.y, Y, fmaf(w.r1.z, Z, w.r1.w)));
+        float Wd = fmaf(w.r2.x, X, fmaf(w.r2.y, Y, fmaf(w.r2.z, Z, w.r2.w)));
+        good = (Wd > 1.0f);
+        float u = good ? U / Wd + w.pp.x : 0.0f, v = good ? Vv / Wd + w.pp.y : 0.0f;
+        umin = umax = u;
+        vmin = vmax = v;
+      }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        umin = fminf(umin, __shfl_xor_sync(0xffffffffu, umin, o));
+        umax = fmaxf(umax, __shfl_xor_sync(0xffffffffu, umax, o));
+        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        good &= __shfl_xor_sync(0xffffffffu, good, o);
+      }
+      if (vi < nvc && cr == 0) {
+        int4 t = make_int4(0, 0, FP_GLOBAL, TB_BWW);
+        if (good && fabsf(umin) < 1e6f && fabsf(umax) < 1e6f && fabsf(vmin) < 1e6f &&
+            fabsf(vmax) < 1e6f) {
+          int x0 = (int)floorf(umin) - 1, x1 = (int)floorf(umax) + 2;
+          int r0 = (int)floorf(vmin) - 1, r1 = (int)floorf(vmax) + 2;
+          if (x1 < 0 || x0 >= a.W || r1 < 0 || r0 >= a.H)
+            t = make_int4(x0, r0, FP_SKIP, 0);
+          else if (r1 - r0 + 1 <= TB_BH && x1 - x0 + 1 <= TB_BWW)
+            t = make_int4(x0, r0, FP_WIDE, x1 - x0 + 1);
+        }
+        vtab[vi] = t;
+      }
+    }
+    __syncthreads();
+    for (int vi = 0; vi < nvc; ++vi) {
+      int4 t = vtab[vi];
+      if (t.z == FP_SKIP) continue;
+      const dc::BPView w = sv[vi];
+      float *img = gbase + (size_t)(c0 + vi) * np;
+      float U0 = fmaf(w.r0.x, xo, fmaf(w.r0.y, yo, fmaf(w.r0.z, zo, w.r0.w)));
+      float V0 = fmaf(w.r1.x, xo, fmaf(w.r1.y, yo, fmaf(w.r1.z, zo, w.r1.w)));
+      float W0 = fmaf(w.r2.x, xo, fmaf(w.r2.y, yo, fmaf(w.r2.z, zo, w.r2.w)));
+      float dU = w.r0.z * a.dz, dV = w.r1.z * a.dz, dW = w.r2.z * a.dz;
+      float ex = w.ca.x + xo, ey = w.ca.y + yo, ez0 = w.ca.z + zo;
+      float rho2 = fmaf(ex, ex, ey * ey);
+      // fixed-point unit of this (box, view); CTA-uniform
+      float dcx = w.ca.x + bcx, dcy = w.ca.y + bcy, dcz = w.ca.z + bcz;
+      float dmin = sqrtf(dcx * dcx + dcy * dcy + dcz * dcz) - bhd;
+      if (t.z == FP_WIDE && !(dmin > 1.0f)) t.z = FP_GLOBAL;
+      if (t.z == FP_WIDE) {
+        const float bound = gsum / (dmin * dmin);             // >= any pixel sum
+        const float to_fix = 1073741824.0f / bound;            // bound -> 2^30
+        const float from_fix = bound * (1.0f / 1073741824.0f);
+        const float cul = w.pp.x - (float)t.x, cvl = w.pp.y - (float)t.y;
+        const float umx = (float)TB_BWW - 1.001f, vmx = (float)TB_BH - 1.001f;
+        if (any) {
+#pragma unroll
+          for (int k = 0; k < TB_NZ; ++k) {
+            if (gv[k] == 0.0f) continue;
+            float kf = (float)k;
+            float rw = dc::rcp_approx(fmaf(kf, dW, W0));
+            float u = fminf(fmaxf(fmaf(fmaf(kf, dU, U0), rw, cul), 0.0f), umx);
+            float v = fminf(fmaxf(fmaf(fmaf(kf, dV, V0), rw, cvl), 0.0f), vmx);
+            float ez = fmaf(kf, a.dz, ez0);
+            float gk = gv[k] * dc::rcp_approx(fmaf(ez, ez, rho2)) * to_fix;
+            float fu, fv;
+            int j = dc::floor_frac(u, fu), r = dc::floor_frac(v, fv);
+            int *p = tile + r * TA_S + j;
+            float g1 = gk * fv, g0 = gk - g1;
+            float g01 = g0 * fu, g11 = g1 * fu;
+            atomicAdd(p, __float2int_rn(g0 - g01));
+            atomicAdd(p + 1, __float2int_rn(g01));
+            atomicAdd(p + TA_S, __float2int_rn(g1 - g11));
+            atomicAdd(p + TA_S + 1, __float2int_rn(g11));
+          }
+        }
+        __syncthreads();
+        // flush the whole tile (pixels inside the detector) and clear it
+        for (int e = tid; e < TB_BH * TB_BWW; e += TB_TX * TB_TY) {
+          int r = e >> 6, c = e & 63;
+          int q = tile[r * TA_S + c];
+          if (q != 0) {
+            tile[r * TA_S + c] = 0;
+            int jj = t.x + c, rr = t.y + r;
+            if (jj >= 0 && jj < a.W && rr >= 0 && rr < a.H)
+              atomicAdd(img + (size_t)rr * a.W + jj, (float)q * from_fix);
+          }
+        }
+        __syncthreads();
+      } else if (any) {
+#pragma unroll
+        for (int k = 0; k < TB_NZ; ++k) {
+          if (gv[k] == 0.0f) continue;
+          float kf = (float)k;
+          float dep = fmaf(kf, dW, W0);
+          if (!(dep > 0.0f)) continue;
+          float rw = __frcp_rn(dep);
+          float u = fmaf(fmaf(kf, dU, U0), rw, w.pp.x);
+          float v = fmaf(fmaf(kf, dV, V0), rw, w.pp.y);
+          float ez = fmaf(kf, a.dz, ez0);
+          float g = gv[k] * __frcp_rn(fmaf(ez, ez, rho2));
+          u = fminf(fmaxf(u, -2.0f), (float)a.W + 1.0f);
+          v = fminf(fmaxf(v, -2.0f), (float)a.H + 1.0f);
+          float fu, fv;
+          int j = dc::floor_frac(u, fu), r = dc::floor_frac(v, fv);
+          bool j0 = (j >= 0 && j < a.W), j1 = (j + 1 >= 0 && j + 1 < a.W);
+          bool r0 = (r >= 0 && r < a.H), r1 = (r + 1 >= 0 && r + 1 < a.H);
+          float *p = img + (ptrdiff_t)r * a.W + j;
+          if (r0 && j0) atomicAdd(p, g * (1.0f - fu) * (1.0f - fv));
+          if (r0 && j1) atomicAdd(p + 1, g * fu * (1.0f - fv));
+          if (r1 && j0) atomicAdd(p + a.W, g * (1.0f - fu) * fv);
+          if (r1 && j1) atomicAdd(p + a.W + 1, g * fu * fv);
+        }
+      }
+    }
   }
 }
 
@@ -504,25 +796,43 @@ bool make_map(CUtensorMap *m, const void *base, int dtype, int W, int H, long lo
   return r == CUDA_SUCCESS;
 }
 
+template <typename T, int NZ>
+int launch_bp_tma_nz(const dc_geometry *g, BPArgs &a, bool kahan, cudaStream_t st,
+                     const CUtensorMap &mn, const CUtensorMap &mw) {
+  dim3 blk(TB_TX, TB_TY);
+  dim3 grid((a.nx + TB_TX - 1) / TB_TX, (a.ny + TB_TY - 1) / TB_TY,
+            ((a.nz + NZ - 1) / NZ) * a.B);
+  const size_t sm = bp_tma_smem<T>();
+  if (kahan) {
+    DC_CUDA(cudaFuncSetAttribute(k_bp3d_tma<T, true, NZ>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_bp3d_tma<T, true, NZ><<<grid, blk, sm, st>>>(a, g->w_flags, mn, mw);
+  } else {
+    DC_CUDA(cudaFuncSetAttribute(k_bp3d_tma<T, false, NZ>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_bp3d_tma<T, false, NZ><<<grid, blk, sm, st>>>(a, g->w_flags, mn, mw);
+  }
+  return DC_OK;
+}
+
+bool tma_ok(const void *base, int W, int dtype) {
+  int es = (dtype == DC_F32) ? 4 : 2;
+  return ((size_t)W * es) % 16 == 0 && ((uintptr_t)base & 15) == 0 && encode_fn() != nullptr;
+}
+
 template <typename T>
 int launch_bp_tma(const dc_geometry *g, BPArgs &a, int dtype, bool kahan, cudaStream_t st,
                   bool *used) {
   *used = false;
-  int es = (dtype == DC_F32) ? 4 : 2;
-  if (((size_t)a.W * es) % 16 != 0 || ((uintptr_t)a.gF & 15) != 0) return DC_OK;
-  if (getenv("DC_BP_NO_TMA")) return DC_OK;
+  if (!tma_ok(a.gF, a.W, dtype) || getenv("DC_BP_NO_TMA")) return DC_OK;
   CUtensorMap mn, mw;
   long long nimg = (long long)a.B * a.V;
   if (!make_map(&mn, a.gF, dtype, a.W, a.H, nimg, TB_BWN) ||
       !make_map(&mw, a.gF, dtype, a.W, a.H, nimg, TB_BWW))
     return DC_OK;
-  dim3 blk(TB_TX, TB_TY);
-  dim3 grid((a.nx + TB_TX - 1) / TB_TX, (a.ny + TB_TY - 1) / TB_TY,
-            ((a.nz + TB_NZ - 1) / TB_NZ) * a.B);
-  if (kahan)
-    k_bp3d_tma<T, true><<<grid, blk, 0, st>>>(a, g->w_flags, mn, mw);
-  else
-    k_bp3d_tma<T, false><<<grid, blk, 0, st>>>(a, g->w_flags, mn, mw);
+  int rc = (g->bp_nz == 16) ? launch_bp_tma_nz<T, 16>(g, a, kahan, st, mn, mw)
+                            : launch_bp_tma_nz<T, 32>(g, a, kahan, st, mn, mw);
+  if (rc) return rc;
   *used = true;
   return DC_OK;
 }
@@ -634,8 +944,237 @@ int dc_backproject_adjoint(const dc_geometry *g, int B, const float *grad_vol,
   dim3 grid((d.vol_x + BP_TX - 1) / BP_TX, (d.vol_y + BP_TY - 1) / BP_TY,
             ((d.vol_z + BP_NZ - 1) / BP_NZ) * B);
   dc::ProfScope ps(dc::KID_BP3D_ADJ, st);
-  k_bp3d_adj<<<grid, blk, 0, st>>>(a);
+  if (getenv("DC_BP_ADJ_GLOBAL")) {
+    k_bp3d_adj<<<grid, blk, 0, st>>>(a);
+  } else {
+    dim3 gridt((d.vol_x + TB_TX - 1) / TB_TX, (d.vol_y + TB_TY - 1) / TB_TY,
+               ((d.vol_z + TB_NZ - 1) / TB_NZ) * B);
+    k_bp3d_adj_tile<<<gridt, blk, 0, st>>>(a);
+  }
   DC_CHECK_LAUNCH("k_bp3d_adj");
+  return DC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------
+// Batched reconstruction: per-problem filters, then one persistent
+// backprojection over all problems.  Everything a run needs is allocated by
+// dc_batch_create, so dc_batch_run allocates nothing and can be captured in
+// a CUDA graph.
+struct dc_batch {
+  int n;
+  int dtype;
+  unsigned flags;
+  int nz;
+  int grid;
+  long long total;
+  int order[DC_MAX_BATCH];        // table position -> problem index
+  dc_geometry *geoms[DC_MAX_BATCH];
+  void *gF[DC_MAX_BATCH];         // owned filtered projections [V][H][W]
+  float *scale[DC_MAX_BATCH];     // owned FP16 scales [V]
+  BatchProblem *d_probs;
+  CUtensorMap *d_maps;
+  unsigned long long *d_counter;
+};
+
+namespace {
+
+void free_batch(dc_batch *b) {
+  if (!b) return;
+  for (int i = 0; i < b->n; ++i) {
+    cudaFree(b->gF[i]);
+    cudaFree(b->scale[i]);
+  }
+  cudaFree(b->d_probs);
+  cudaFree(b->d_maps);
+  cudaFree(b->d_counter);
+  delete b;
+}
+
+int build_batch_tables(dc_batch *b) {
+  std::vector<BatchProblem> probs(b->n);
+  std::vector<CUtensorMap> maps(2 * b->n);
+  long long first = 0;
+  for (int t = 0; t < b->n; ++t) {
+    int i = b->order[t];
+    const dc_geometry *g = b->geoms[i];
+    const dc_geometry_desc &d = g->d;
+    BatchProblem &P = probs[t];
+    memset(&P, 0, sizeof(P));
+    P.a.gF = b->gF[i];
+    P.a.scale = (b->dtype == DC_F16) ? b->scale[i] : nullptr;
+    P.a.views = g->bpv;
+    P.a.vol = nullptr;
+    P.a.flags = b->flags & ~DC_KAHAN;
+    P.a.V = d.n_views;
+    P.a.H = d.det_rows;
+    P.a.W = d.det_cols;
+    P.a.nx = d.vol_x;
+    P.a.ny = d.vol_y;
+    P.a.nz = d.vol_z;
+    P.a.B = 1;
+    P.a.dx = (float)d.voxel[0];
+    P.a.dy = (float)d.voxel[1];
+    P.a.dz = (float)d.voxel[2];
+    if (!make_map(&maps[2 * t], b->gF[i], b->dtype, d.det_cols, d.det_rows, d.n_views, TB_BWN) ||
+        !make_map(&maps[2 * t + 1], b->gF[i], b->dtype, d.det_cols, d.det_rows, d.n_views,
+                  TB_BWW))
+      return dc::fail(DC_ERR_CUDA, "dc_batch: tensor map encoding failed");
+    P.tmn = b->d_maps + 2 * t;
+    P.tmw = b->d_maps + 2 * t + 1;
+    P.bx = (d.vol_x + TB_TX - 1) / TB_TX;
+    P.by = (d.vol_y + TB_TY - 1) / TB_TY;
+    P.bz = (d.vol_z + b->nz - 1) / b->nz;
+    P.first = first;
+    first += (long long)P.bx * P.by * P.bz;
+  }
+  b->total = first;
+  DC_CUDA(cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                     cudaMemcpyHostToDevice));
+  DC_CUDA(cudaMemcpy(b->d_probs, probs.data(), sizeof(BatchProblem) * probs.size(),
+                     cudaMemcpyHostToDevice));
+  return DC_OK;
+}
+
+template <typename T, bool KAHAN, int NZ>
+int launch_batched(dc_batch *b, BatchRun &run, cudaStream_t st) {
+  const size_t sm = bp_tma_smem<T>();
+  DC_CUDA(cudaFuncSetAttribute(k_bp3d_batched<T, KAHAN, NZ>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_bp3d_batched<T, KAHAN, NZ><<<b->grid, dim3(TB_TX, TB_TY), sm, st>>>(
+      b->d_probs, b->n, b->total, b->d_counter, b->geoms[0]->w_flags, run);
+  return DC_OK;
+}
+
+template <typename T>
+int launch_batched_t(dc_batch *b, BatchRun &run, cudaStream_t st) {
+  bool kahan = (b->flags & DC_KAHAN) != 0;
+  if (b->nz == 16)
+    return kahan ? launch_batched<T, true, 16>(b, run, st) : launch_batched<T, false, 16>(b, run, st);
+  return kahan ? launch_batched<T, true, 32>(b, run, st) : launch_batched<T, false, 32>(b, run, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int dc_batch_create(int n, dc_geometry *const *geoms, int dtype, unsigned flags,
+                    dc_batch **out) {
+  if (!out || !geoms) return dc::fail(DC_ERR_ARG, "dc_batch_create: NULL argument");
+  *out = nullptr;
+  if (n < 1 || n > DC_MAX_BATCH)
+    return dc::fail(DC_ERR_ARG, "dc_batch_create: 1 <= n <= " + std::to_string(DC_MAX_BATCH));
+  if (dtype != DC_F32 && dtype != DC_BF16 && dtype != DC_F16)
+    return dc::fail(DC_ERR_ARG, "dc_batch_create: unknown dtype");
+  if (flags & ~(DC_KAHAN | DC_RELU))
+    return dc::fail(DC_ERR_ARG, "dc_batch_create: flags may be DC_KAHAN | DC_RELU");
+  if (!encode_fn()) return dc::fail(DC_ERR_UNSUPPORTED, "dc_batch_create: no TMA encoder");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  int es = (dtype == DC_F32) ? 4 : 2;
+  for (int i = 0; i < n; ++i) {
+    if (!geoms[i]) return dc::fail(DC_ERR_ARG, "dc_batch_create: NULL geometry");
+    if (geoms[i]->device != dev)
+      return dc::fail(DC_ERR_ARG, "dc_batch_create: geometry on another device");
+    if (((size_t)geoms[i]->d.det_cols * es) % 16 != 0)
+      return dc::fail(DC_ERR_UNSUPPORTED,
+                      "dc_batch_create: detector rows must be a multiple of 16 bytes");
+  }
+  dc_batch *b = new dc_batch();
+  memset((void *)b, 0, sizeof(dc_batch));
+  b->n = n;
+  b->dtype = dtype;
+  b->flags = flags;
+  b->nz = 32;
+  for (int i = 0; i < n; ++i) b->geoms[i] = geoms[i];
+  // largest view count first
+  for (int i = 0; i < n; ++i) b->order[i] = i;
+  std::sort(b->order, b->order + n, [&](int x, int y) {
+    return geoms[x]->d.n_views > geoms[y]->d.n_views;
+  });
+  auto bail = [&](int code) {
+    free_batch(b);
+    return code;
+  };
+  for (int i = 0; i < n; ++i) {
+    const dc_geometry_desc &d = geoms[i]->d;
+    size_t bytes = (size_t)d.n_views * d.det_rows * d.det_cols * es;
+    cudaError_t e = dc::dmalloc(&b->gF[i], bytes);
+    if (e != cudaSuccess) return bail(dc::cuda_fail(e, "dc_batch_create: g^F"));
+    if (dtype == DC_F16) {
+      e = dc::dmalloc((void **)&b->scale[i], sizeof(float) * d.n_views);
+      if (e != cudaSuccess) return bail(dc::cuda_fail(e, "dc_batch_create: scales"));
+    }
+  }
+  cudaError_t e = dc::dmalloc((void **)&b->d_probs, sizeof(BatchProblem) * n);
+  if (e == cudaSuccess) e = dc::dmalloc((void **)&b->d_maps, sizeof(CUtensorMap) * 2 * n);
+  if (e == cudaSuccess) e = dc::dmalloc((void **)&b->d_counter, sizeof(unsigned long long));
+  if (e != cudaSuccess) return bail(dc::cuda_fail(e, "dc_batch_create: tables"));
+  int rc = build_batch_tables(b);
+  if (rc) return bail(rc);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->grid = std::max(1, sms) * 2;
+  *out = b;
+  return DC_OK;
+}
+
+int dc_batch_set_bp_nz(dc_batch *b, int nz) {
+  if (!b || (nz != 16 && nz != 32))
+    return dc::fail(DC_ERR_ARG, "dc_batch_set_bp_nz: nz must be 16 or 32");
+  if (b->nz == nz) return DC_OK;
+  b->nz = nz;
+  return build_batch_tables(b);
+}
+
+int dc_batch_run(dc_batch *b, const float *const *g, const float *const *W, float *const *vol,
+                 void *stream) {
+  if (!b || !g || !vol) return dc::fail(DC_ERR_ARG, "dc_batch_run: NULL argument");
+  for (int i = 0; i < b->n; ++i)
+    if (!g[i] || !vol[i]) return dc::fail(DC_ERR_ARG, "dc_batch_run: NULL g or vol");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < b->n; ++i) {
+    int rc = dc_filter(b->geoms[i], 1, g[i], W ? W[i] : nullptr, b->gF[i], b->dtype,
+                       b->scale[i], stream);
+    if (rc) return rc;
+  }
+  BatchRun run;
+  memset(&run, 0, sizeof(run));
+  for (int t = 0; t < b->n; ++t) run.vol[t] = vol[b->order[t]];
+  DC_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), st));
+  dc::ProfScope ps(dc::KID_BP3D, st);
+  int rc = DC_OK;
+  switch (b->dtype) {
+    case DC_F32: rc = launch_batched_t<float>(b, run, st); break;
+    case DC_BF16: rc = launch_batched_t<__nv_bfloat16>(b, run, st); break;
+    default: rc = launch_batched_t<__half>(b, run, st); break;
+  }
+  if (rc) return rc;
+  DC_CHECK_LAUNCH("k_bp3d_batched");
+  return DC_OK;
+}
+
+void dc_batch_destroy(dc_batch *b) { free_batch(b); }
+
+int dc_geometry_set_tuning(dc_geometry *g, int chunk_images, int bp_nz) {
+  if (!g) return dc::fail(DC_ERR_ARG, "dc_geometry_set_tuning: NULL geometry");
+  if (chunk_images < 0 || chunk_images > g->chunk_capacity)
+    return dc::fail(DC_ERR_ARG, "dc_geometry_set_tuning: chunk_images must be in [1, " +
+                                    std::to_string(g->chunk_capacity) + "] (0 keeps it)");
+  if (bp_nz != 0 && bp_nz != 16 && bp_nz != 32)
+    return dc::fail(DC_ERR_ARG, "dc_geometry_set_tuning: bp_nz must be 16 or 32 (0 keeps it)");
+  if (chunk_images > 0) g->chunk_images = chunk_images;
+  if (bp_nz > 0) g->bp_nz = bp_nz;
+  return DC_OK;
+}
+
+int dc_geometry_get_tuning(const dc_geometry *g, int *chunk_images, int *chunk_capacity,
+                           int *bp_nz) {
+  if (!g) return dc::fail(DC_ERR_ARG, "dc_geometry_get_tuning: NULL geometry");
+  if (chunk_images) *chunk_images = g->chunk_images;
+  if (chunk_capacity) *chunk_capacity = g->chunk_capacity;
+  if (bp_nz) *bp_nz = g->bp_nz;
   return DC_OK;
 }
 

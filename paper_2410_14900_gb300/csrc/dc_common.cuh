@@ -75,10 +75,27 @@ struct FView {
   float ay, az, pad0, pad1;
 };
 
-// FP32 per-angle record: (cos, sin, joseph scale p/max(|c|,|s|), hat inverse
-// half-width ds/(p*max(|c|,|s|)))
+// FP32 per-angle record, from FP64 at set-up.  With (cs, sn) = (cos, sin)
+// for the row-stepping Joseph branch and (sin, cos) for the column-stepping
+// one, m = max(|cos|, |sin|) = |cs|:
+//   jscale = p/m, winv = ds/(p m)             Joseph scale, hat half-width^-1
+//   a = (ds/p)/cs, d = -sn/cs                 line-sum position per s-bin, per row
+//   bc = cos p/ds, bs = sin p/ds              s-bin position per pixel column, row
+// Pairs *_hi + *_lo are exact splits whose *_hi has 12 fractional bits, so
+// products with small integers are exact in FP32.
 struct MuRec {
   float c, s, jscale, winv;
+  float a_hi, a_lo, d_hi, d_lo;
+  float dxi, bc_hi, bc_lo, bs_hi;
+  float bs_lo, pad0, pad1, pad2;
+};
+
+// FP32 per-(view, angle) record, from FP64 at set-up: the Joseph position of
+// line s_0 at row 0, b = c_col + c_row sn/cs, and the s-bin position of pixel
+// (0, 0), x = (n_s-1)/2 - (c_u cos + c_v sin) p/ds, each as an integer part
+// and a fraction in [0, 1).
+struct VMu {
+  float b0i, b0f, xoi, xof;
 };
 
 // A group of consecutive angles (all of one Joseph branch) handled by one
@@ -103,6 +120,7 @@ struct dc_geometry {
   dc::BPView *bpv;           // [V]
   dc::FView *fv;             // [V]
   dc::MuRec *mu;             // [n_mu]
+  dc::VMu *vmu;              // [V][n_mu]
   int *mu_order;             // [n_mu] angle index in group order
   dc::MuGroup *groups;       // [n_groups]
   int n_groups;
@@ -110,6 +128,8 @@ struct dc_geometry {
   int mg;                    // max angles per group
   // work area
   int chunk_images;          // images (view x batch item) per chunk
+  int chunk_capacity;        // images the work area was sized for
+  int bp_nz;                 // voxels per thread along z in the backprojector (16, 32)
   size_t img_stride;         // floats per padded image  (H * Wp)
   size_t imgT_stride;        // floats per padded transposed image (W * Hp)
   size_t sino_stride;        // floats per padded sinogram (n_mu * NSp)
@@ -127,5 +147,53 @@ namespace dc {
 // host-side helpers defined in dc_filter.cu / dc_backproject.cu
 int alloc_workspace(dc_geometry *g);
 int build_mu_tables(dc_geometry *g);
+// FP64 split of v into hi (12 fractional bits) + lo
+inline __host__ __device__ float split_hi12(double v) {
+  return (float)(rint(v * 4096.0) / 4096.0);
+}
+
+// The per-angle record of angle m = mu_m / (pi / n_mu), from FP64 (host or
+// device).  The Joseph branch is decided exactly: 4m <= n_mu or 4m >= 3 n_mu
+// steps over rows (|cos| >= |sin|, ties included).
+inline __host__ __device__ MuRec make_mu_rec(int m, int n_mu, double pitch, double ds) {
+  double ang = m * 3.14159265358979323846 / n_mu, c = cos(ang), s = sin(ang);
+  bool rows = (4 * m <= n_mu) || (4 * m >= 3 * n_mu);
+  double cs = rows ? c : s, sn = rows ? s : c;
+  double mx = fabs(cs);
+  MuRec r;
+  r.c = (float)c;
+  r.s = (float)s;
+  r.jscale = (float)(pitch / mx);
+  r.winv = (float)(ds / (pitch * mx));
+  double A = (ds / pitch) / cs, dx = -sn / cs, bc = c * pitch / ds, bs = s * pitch / ds;
+  r.a_hi = split_hi12(A);
+  r.a_lo = (float)(A - (double)r.a_hi);
+  r.d_hi = split_hi12(dx);
+  r.d_lo = (float)(dx - (double)r.d_hi);
+  r.dxi = (float)dx;
+  r.bc_hi = split_hi12(bc);
+  r.bc_lo = (float)(bc - (double)r.bc_hi);
+  r.bs_hi = split_hi12(bs);
+  r.bs_lo = (float)(bs - (double)r.bs_hi);
+  r.pad0 = r.pad1 = r.pad2 = 0.0f;
+  return r;
+}
+
+// the FP64 origins of one (view, angle): see VMu
+inline __host__ __device__ VMu make_vmu(int m, int n_mu, int n_s, double pitch, double ds,
+                                        double cu, double cv) {
+  double ang = m * 3.14159265358979323846 / n_mu, c = cos(ang), s = sin(ang);
+  bool rows = (4 * m <= n_mu) || (4 * m >= 3 * n_mu);
+  double cs = rows ? c : s, sn = rows ? s : c;
+  double ccol = rows ? cu : cv, crow = rows ? cv : cu;
+  double b0 = ccol + crow * sn / cs;
+  double xo = 0.5 * (n_s - 1) - (cu * c + cv * s) * pitch / ds;
+  VMu r;
+  r.b0i = (float)floor(b0);
+  r.b0f = (float)(b0 - floor(b0));
+  r.xoi = (float)floor(xo);
+  r.xof = (float)(xo - floor(xo));
+  return r;
+}
 
 }  // namespace dc

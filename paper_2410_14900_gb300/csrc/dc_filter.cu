@@ -98,6 +98,7 @@ struct LineArgs {
   int b0;               // first batch item of the chunk
   float pitch, ds, cT;  // cT = (pi/n_mu) ds / pitch^2
   const dc::MuRec *mu;
+  const dc::VMu *vmu;   // [V][n_mu]
   const int *mu_order;
   const dc::MuGroup *groups;
   const dc::FView *fv;
@@ -109,7 +110,7 @@ struct LineArgs {
   int mg;              // max angles per group
 };
 
-// per-angle constants of one CTA, computed in FP64 and stored as float pairs
+// per-angle constants of one CTA (from the set-up tables)
 struct LineMu {
   float b0i, b0f;    // c_col + c_row sn/cs  = b0i (integer) + b0f
   float a_hi, a_lo;  // (ds/p)/cs  (hi has 12 fractional bits)
@@ -118,12 +119,8 @@ struct LineMu {
   float jscale;      // p / |cs|
 };
 
-__device__ __forceinline__ float split_hi(double v) {
-  return (float)(rint(v * 4096.0) / 4096.0);
-}
-
 template <int MODE>
-__global__ void __launch_bounds__(LS_THREADS) k_linesum(LineArgs a) {
+__global__ void __launch_bounds__(LS_THREADS, 2) k_linesum(LineArgs a) {
   constexpr bool DIFF = (MODE != M_RAW);
   constexpr int STRIDE_L = DIFF ? 31 : 32;  // lines per task (diff: one overlap)
   extern __shared__ __align__(16) float smem[];
@@ -156,22 +153,17 @@ __global__ void __launch_bounds__(LS_THREADS) k_linesum(LineArgs a) {
   }
   if (threadIdx.x < G.count) {
     int m = a.mu_order[G.first + threadIdx.x];
-    double ang = (double)m * 3.14159265358979323846 / a.n_mu;
-    double cm = cos(ang), sm = sin(ang);
-    double cs = G.branch ? sm : cm, sn = G.branch ? cm : sm;
-    double ccol = G.branch ? fv.cv : fv.cu, crow = G.branch ? fv.cu : fv.cv;
-    double b0 = ccol + crow * sn / cs;
-    double A = ((double)a.ds / a.pitch) / cs;
-    double dx = -sn / cs;
+    const dc::MuRec R = a.mu[m];
+    const dc::VMu Q = a.vmu[(size_t)v * a.n_mu + m];
     LineMu L;
-    L.b0i = (float)floor(b0);
-    L.b0f = (float)(b0 - floor(b0));
-    L.a_hi = split_hi(A);
-    L.a_lo = (float)(A - (double)L.a_hi);
-    L.d_hi = split_hi(dx);
-    L.d_lo = (float)(dx - (double)L.d_hi);
-    L.dxi = (float)dx;
-    L.jscale = (float)((double)a.pitch / fabs(cs));
+    L.b0i = Q.b0i;
+    L.b0f = Q.b0f;
+    L.a_hi = R.a_hi;
+    L.a_lo = R.a_lo;
+    L.d_hi = R.d_hi;
+    L.d_lo = R.d_lo;
+    L.dxi = R.dxi;
+    L.jscale = R.jscale;
     lmu[threadIdx.x] = L;
   }
   // zero the row pads of both stages (never written by the bulk copies)
@@ -258,19 +250,21 @@ __global__ void __launch_bounds__(LS_THREADS) k_linesum(LineArgs a) {
       const float *base = st + PADL + J;
       float sum = 0.0f;
       if (__all_sync(0xffffffffu, inside)) {
+        float qf = 0.0f;
 #pragma unroll 4
-        for (int q = 0; q < nr; ++q) {
-          float x = fmaf((float)q, dxi, fb), f;
-          int j = dc::floor_frac(x, f);
+        for (int q = 0; q < nr; ++q, qf += 1.0f) {
+          float f;
+          int j = dc::floor_frac(fmaf(qf, dxi, fb), f);
           const float *p = base + q * rstride + j;
           float g0 = p[0], g1 = p[1];
           sum += fmaf(f, g1 - g0, g0);
         }
       } else {
+        float qf = 0.0f;
 #pragma unroll 4
-        for (int q = 0; q < nr; ++q) {
-          float x = fminf(fmaxf(fmaf((float)q, dxi, fb), lo), hi), f;
-          int j = dc::floor_frac(x, f);
+        for (int q = 0; q < nr; ++q, qf += 1.0f) {
+          float f;
+          int j = dc::floor_frac(fminf(fmaxf(fmaf(qf, dxi, fb), lo), hi), f);
           const float *p = base + q * rstride + j;
           float g0 = p[0], g1 = p[1];
           sum += fmaf(f, g1 - g0, g0);
@@ -419,6 +413,8 @@ struct BP2Args {
   int b0;
   float pitch, ds;
   const dc::FView *fv;
+  const dc::MuRec *mu;
+  const dc::VMu *vmu;  // [V][n_mu]
   int weight;          // WT_NONE / WT_COS / WT_D
   int out_kind;        // OUT_*
   void *out;           // user [B][V][H][W] (f32 or bf16) or scratch [n][H][Wp] f32
@@ -468,25 +464,32 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
   // per-angle constants (FP64 once per CTA and angle): xi(j, r) = position of
   // pixel (j, r) on the s grid, in s-bin units; xi(j0+jl, r0+rl) =
   // I00 + F00 + jl*Bc + rl*Bs
+  // per-angle constants of this tile (FP32 from exact splits): the s-bin
+  // position of pixel (j0 + jl, r0 + rl) is I00 + F00 + jl*Bc + rl*Bs; pad0
+  // flags angles whose positions stay inside the clamp range over the tile
   auto angle_consts = [&](int c) {
     int mi = threadIdx.x;
     int m = c * BP2_MC + mi;
     if (mi < BP2_MC && m < a.n_mu) {
-      double ang = (double)m * 3.14159265358979323846 / a.n_mu;
-      double cm = cos(ang), sm = sin(ang);
-      double k = (double)a.pitch / a.ds;
-      double xi = 0.5 * (a.n_s - 1) + ((j0 - (double)fv.cu) * cm + (r0 - (double)fv.cv) * sm) * k;
-      double fl = floor(xi);
-      // the Joseph branch decides the hat half-width p * max(|cos|, |sin|)
-      bool rowsb = (4 * m <= a.n_mu) || (4 * m >= 3 * a.n_mu);
-      double mx = rowsb ? fabs(cm) : fabs(sm);
+      const dc::MuRec R = a.mu[m];
+      const dc::VMu Q = a.vmu[(size_t)v * a.n_mu + m];
+      float fj0 = (float)j0, fr0 = (float)r0;
+      float t = fj0 * R.bc_hi + fr0 * R.bs_hi;  // exact
+      float ti = floorf(t);
+      float F = Q.xof + (t - ti) + fmaf(fj0, R.bc_lo, fr0 * R.bs_lo);
+      float Fi = floorf(F);
       BPMu M;
-      M.I00 = (float)fl;
-      M.F00 = (float)(xi - fl);
-      M.Bc = (float)(cm * k);
-      M.Bs = (float)(sm * k);
-      M.winv = (float)((double)a.ds / ((double)a.pitch * mx));
-      M.pad0 = M.pad1 = M.pad2 = 0.0f;
+      M.I00 = Q.xoi + ti + Fi;
+      M.F00 = F - Fi;
+      M.Bc = R.bc_hi + R.bc_lo;
+      M.Bs = R.bs_hi + R.bs_lo;
+      M.winv = R.winv;
+      float ex = (float)(BP2_TX - 1) * M.Bc, ey = (float)(BP2_TY - 1) * M.Bs;
+      float xmin = M.F00 + fminf(ex, 0.0f) + fminf(ey, 0.0f);
+      float xmax = M.F00 + fmaxf(ex, 0.0f) + fmaxf(ey, 0.0f);
+      M.pad0 = (xmin >= -1.0f - M.I00 + 0.01f && xmax <= (float)a.n_s - M.I00 - 0.01f) ? 1.0f
+                                                                                          : 0.0f;
+      M.pad1 = M.pad2 = 0.0f;
       bmu[c & 1][mi] = M;
     }
   };
@@ -516,21 +519,36 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
     for (int mi = 0; mi < nm; ++mi) {
       const BPMu M = bmu[c & 1][mi];
       const float *row = st + mi * rstride + PADL + (int)M.I00;
-      float lo = -1.0f - M.I00, hi = (float)a.n_s - M.I00;
       float w1c = 1.0f - M.winv;
+      if (M.pad0 != 0.0f) {
 #pragma unroll
-      for (int ry = 0; ry < BP2_RY; ++ry) {
-        float rt = fmaf(rl0 + (float)ry, M.Bs, M.F00);
+        for (int ry = 0; ry < BP2_RY; ++ry) {
+          float rt = fmaf(rl0 + (float)ry, M.Bs, M.F00);
 #pragma unroll
-        for (int q = 0; q < BP2_NQ; ++q) {
-          float xi = fmaf((float)(lane + 32 * q), M.Bc, rt);
-          xi = fminf(fmaxf(xi, lo), hi);
-          float f;
-          int k = dc::floor_frac(xi, f);
-          const float *p = row + k;
-          float w0 = fmaxf(0.0f, fmaf(-f, M.winv, 1.0f));
-          float w1 = fmaxf(0.0f, fmaf(f, M.winv, w1c));
-          acc[ry][q] = fmaf(w0, p[0], fmaf(w1, p[1], acc[ry][q]));
+          for (int q = 0; q < BP2_NQ; ++q) {
+            float f;
+            int k = dc::floor_frac(fmaf((float)(lane + 32 * q), M.Bc, rt), f);
+            const float *p = row + k;
+            float w0 = fmaxf(0.0f, fmaf(-f, M.winv, 1.0f));
+            float w1 = fmaxf(0.0f, fmaf(f, M.winv, w1c));
+            acc[ry][q] = fmaf(w0, p[0], fmaf(w1, p[1], acc[ry][q]));
+          }
+        }
+      } else {
+        float lo = -1.0f - M.I00, hi = (float)a.n_s - M.I00;
+#pragma unroll
+        for (int ry = 0; ry < BP2_RY; ++ry) {
+          float rt = fmaf(rl0 + (float)ry, M.Bs, M.F00);
+#pragma unroll
+          for (int q = 0; q < BP2_NQ; ++q) {
+            float xi = fminf(fmaxf(fmaf((float)(lane + 32 * q), M.Bc, rt), lo), hi);
+            float f;
+            int k = dc::floor_frac(xi, f);
+            const float *p = row + k;
+            float w0 = fmaxf(0.0f, fmaf(-f, M.winv, 1.0f));
+            float w1 = fmaxf(0.0f, fmaf(f, M.winv, w1c));
+            acc[ry][q] = fmaf(w0, p[0], fmaf(w1, p[1], acc[ry][q]));
+          }
         }
       }
     }
@@ -726,6 +744,7 @@ LineArgs line_args(const dc_geometry *g, int B, int v0, int b0, int n_img) {
   a.ds = (float)d.ds;
   a.cT = (float)((M_PI / d.n_mu) * d.ds / (d.pitch * d.pitch));
   a.mu = g->mu;
+  a.vmu = g->vmu;
   a.mu_order = g->mu_order;
   a.groups = g->groups;
   a.fv = g->fv;
@@ -752,6 +771,8 @@ BP2Args bp2_args(const dc_geometry *g, int B, int v0, int b0, int n_img, const f
   a.pitch = (float)d.pitch;
   a.ds = (float)d.ds;
   a.fv = g->fv;
+  a.mu = g->mu;
+  a.vmu = g->vmu;
   a.Wp = g->Wp;
   a.absmax = g->w_absmax;
   a.err = g->w_flags;
@@ -800,6 +821,8 @@ int alloc_workspace(dc_geometry *g) {
   if (ci < 4) ci = 4;
   if (ci > 256) ci = 256;
   g->chunk_images = ci;
+  g->chunk_capacity = ci;
+  g->bp_nz = 32;
   if (linesum_smem(g) > 200 * 1024 || bp2d_smem(g) > 200 * 1024)
     return fail(DC_ERR_UNSUPPORTED, "detector or sinogram rows too long for shared memory");
   DC_CUDA(dmalloc((void **)&g->w_img, sizeof(float) * g->img_stride * ci));
@@ -1008,11 +1031,12 @@ int dc_sync_status(const dc_geometry *g, void *stream) {
 namespace {
 
 constexpr size_t NA_BYTES = 32u << 20;         // 32 MiB per device
-constexpr size_t NA_TABLE_BYTES = 128u << 10;  // angle tables and error word
+constexpr size_t NA_TABLE_BYTES = 256u << 10;  // angle tables and error word
 constexpr int NA_MAX_MU = 2048;
 constexpr int NA_MAX_DEV = 64;
 
-static_assert((sizeof(dc::MuRec) + sizeof(int) + sizeof(dc::MuGroup)) * NA_MAX_MU + 1024 <=
+static_assert((sizeof(dc::MuRec) + sizeof(dc::VMu) + sizeof(int) + sizeof(dc::MuGroup)) *
+                      NA_MAX_MU + 1024 <=
                   NA_TABLE_BYTES,
               "angle tables overflow their region");
 
@@ -1022,32 +1046,30 @@ static __device__ __align__(256) unsigned char g_na_scratch[NA_BYTES];
 void *g_na_ptr[NA_MAX_DEV];
 std::mutex g_na_mu;
 
-// Angle tables for one call, written into the fixed area by one thread:
-// the same ordering and grouping as the geometry handle's tables.
-__global__ void k_na_tables(int n_mu, int n_s, double pitch, double ds, float cu, float cv,
-                            int mg, dc::MuRec *mu, int *order, dc::MuGroup *groups,
-                            int *n_groups, dc::FView *fv, unsigned *err) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+// Angle tables for one call, written into the fixed area: one thread per
+// angle for the per-angle records, thread 0 for the ordering and grouping
+// (the same as a geometry handle's tables).
+__global__ void k_na_tables(int n_mu, int n_s, double pitch, double ds, double cu, double cv,
+                            int mg, dc::MuRec *mu, dc::VMu *vmu, int *order,
+                            dc::MuGroup *groups, dc::FView *fv, unsigned *err) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < n_mu) {
+    mu[m] = dc::make_mu_rec(m, n_mu, pitch, ds);
+    vmu[m] = dc::make_vmu(m, n_mu, n_s, pitch, ds, cu, cv);
+  }
+  if (m != 0) return;
   *err = 0u;
   dc::FView f;
   f.D = 1.0f;
-  f.cu = cu;
-  f.cv = cv;
+  f.cu = (float)cu;
+  f.cv = (float)cv;
   f.ax = f.ay = f.az = f.pad0 = f.pad1 = 0.0f;
   *fv = f;
   int nord = 0, ng = 0;
   for (int br = 0; br < 2; ++br) {
     int cnt = 0;
-    for (int m = 0; m < n_mu; ++m) {
-      double ang = m * 3.14159265358979323846 / n_mu, c = cos(ang), s = sin(ang);
-      bool rows = (4 * m <= n_mu) || (4 * m >= 3 * n_mu);
-      if (br == 0) {
-        double mx = rows ? fabs(c) : fabs(s);
-        mu[m].c = (float)c;
-        mu[m].s = (float)s;
-        mu[m].jscale = (float)(pitch / mx);
-        mu[m].winv = (float)(ds / (pitch * mx));
-      }
+    for (int q = 0; q < n_mu; ++q) {
+      bool rows = (4 * q <= n_mu) || (4 * q >= 3 * n_mu);
       if ((br == 0) != rows) continue;
       if (cnt % mg == 0) {
         groups[ng].first = nord;
@@ -1057,11 +1079,10 @@ __global__ void k_na_tables(int n_mu, int n_s, double pitch, double ds, float cu
         ++ng;
       }
       groups[ng - 1].count += 1;
-      order[nord++] = m;
+      order[nord++] = q;
       ++cnt;
     }
   }
-  *n_groups = ng;
 }
 
 }  // namespace
@@ -1109,17 +1130,19 @@ extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, do
   }
   // fixed-area layout: tables first, then the image copies
   dc::MuRec *mu = (dc::MuRec *)base;
-  int *order = (int *)(base + sizeof(dc::MuRec) * NA_MAX_MU);
-  dc::MuGroup *groups = (dc::MuGroup *)(base + (sizeof(dc::MuRec) + sizeof(int)) * NA_MAX_MU);
-  unsigned char *tail = base + (sizeof(dc::MuRec) + sizeof(int) + sizeof(dc::MuGroup)) * NA_MAX_MU;
-  int *n_groups = (int *)tail;
-  dc::FView *fv = (dc::FView *)(tail + 256);
-  unsigned *err = (unsigned *)(tail + 512);
+  dc::VMu *vmu = (dc::VMu *)(base + sizeof(dc::MuRec) * NA_MAX_MU);
+  int *order = (int *)(base + (sizeof(dc::MuRec) + sizeof(dc::VMu)) * NA_MAX_MU);
+  dc::MuGroup *groups =
+      (dc::MuGroup *)(base + (sizeof(dc::MuRec) + sizeof(dc::VMu) + sizeof(int)) * NA_MAX_MU);
+  unsigned char *tail =
+      base + (sizeof(dc::MuRec) + sizeof(dc::VMu) + sizeof(int) + sizeof(dc::MuGroup)) * NA_MAX_MU;
+  dc::FView *fv = (dc::FView *)tail;
+  unsigned *err = (unsigned *)(tail + 256);
   float *work = (float *)(base + NA_TABLE_BYTES);
 
   cudaStream_t st = (cudaStream_t)stream;
-  k_na_tables<<<1, 1, 0, st>>>(n_mu, n_s, pitch, ds, (float)cu, (float)cv, mg, mu, order,
-                               groups, n_groups, fv, err);
+  k_na_tables<<<(n_mu + 127) / 128, 128, 0, st>>>(n_mu, n_s, pitch, ds, cu, cv, mg, mu, vmu,
+                                                  order, groups, fv, err);
   DC_CHECK_LAUNCH("k_na_tables");
   // the group count is a host-side launch parameter: recompute it here
   int nb0 = 0, nb1 = 0;
@@ -1175,6 +1198,7 @@ extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, do
     a.pitch = (float)pitch;
     a.ds = (float)ds;
     a.mu = mu;
+    a.vmu = vmu;
     a.mu_order = order;
     a.groups = groups;
     a.fv = fv;

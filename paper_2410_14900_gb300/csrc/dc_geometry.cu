@@ -140,12 +140,24 @@ __global__ void k_geometry_tables(int V, int closed, double pitch, double cx, do
   fv[i] = r;
 }
 
+// One thread per (view, angle): FP64 origins of the line-sum and pixel
+// gathers (the principal point enters here).
+__global__ void k_geometry_angles(int V, int n_mu, int n_s, double pitch, double ds,
+                                  const double *__restrict__ geo, dc::VMu *__restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= V * n_mu) return;
+  int i = t / n_mu, m = t % n_mu;
+  const double *g = geo + (size_t)GN * i;
+  out[t] = dc::make_vmu(m, n_mu, n_s, pitch, ds, g[13], g[14]);
+}
+
 void free_geometry(dc_geometry *g) {
   if (!g) return;
   cudaFree(g->geo64);
   cudaFree(g->bpv);
   cudaFree(g->fv);
   cudaFree(g->mu);
+  cudaFree(g->vmu);
   cudaFree(g->mu_order);
   cudaFree(g->groups);
   cudaFree(g->w_img);
@@ -172,13 +184,8 @@ int build_mu_tables(dc_geometry *g) {
   std::vector<MuRec> mu(n_mu);
   std::vector<int> b0, b1;
   for (int m = 0; m < n_mu; ++m) {
-    double ang = m * M_PI / n_mu, c = cos(ang), s = sin(ang);
     bool rows = (4 * m <= n_mu) || (4 * m >= 3 * n_mu);
-    double mx = rows ? fabs(c) : fabs(s);
-    mu[m].c = (float)c;
-    mu[m].s = (float)s;
-    mu[m].jscale = (float)(d.pitch / mx);
-    mu[m].winv = (float)(d.ds / (d.pitch * mx));
+    mu[m] = make_mu_rec(m, n_mu, d.pitch, d.ds);
     (rows ? b0 : b1).push_back(m);
   }
   // angles per group: keep the per-warp task count of the line-sum kernel
@@ -212,6 +219,12 @@ int build_mu_tables(dc_geometry *g) {
   DC_CUDA(cudaMemcpy(g->mu_order, order.data(), sizeof(int) * n_mu, cudaMemcpyHostToDevice));
   DC_CUDA(cudaMemcpy(g->groups, groups.data(), sizeof(MuGroup) * groups.size(),
                      cudaMemcpyHostToDevice));
+  size_t nvm = (size_t)d.n_views * n_mu;
+  DC_CUDA(dmalloc((void **)&g->vmu, sizeof(VMu) * nvm));
+  k_geometry_angles<<<(unsigned)((nvm + 127) / 128), 128>>>(d.n_views, n_mu, d.n_s, d.pitch,
+                                                           d.ds, g->geo64, g->vmu);
+  DC_CUDA(cudaGetLastError());
+  DC_CUDA(cudaDeviceSynchronize());
   return DC_OK;
 }
 
@@ -230,6 +243,9 @@ int dc_setup_geometry(const dc_geometry_desc *desc, const double *P, const doubl
   if (!(d.pitch > 0) || !(d.ds > 0) || !(d.voxel[0] > 0) || !(d.voxel[1] > 0) ||
       !(d.voxel[2] > 0))
     return dc::fail(DC_ERR_ARG, "dc_setup_geometry: spacings must be positive");
+  if (d.det_rows > 2048 || d.det_cols > 2048 || d.n_s > 2048)
+    return dc::fail(DC_ERR_UNSUPPORTED,
+                    "dc_setup_geometry: detector rows/columns and n_s are limited to 2048");
   if ((long long)d.det_rows * d.det_cols > (1LL << 30) ||
       (long long)d.vol_x * d.vol_y * d.vol_z > (1LL << 34) || d.n_views > (1 << 20) ||
       (long long)d.n_mu * d.n_s > (1LL << 28))

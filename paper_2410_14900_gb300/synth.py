@@ -307,12 +307,15 @@ def voxel_centers(shape_zyx, voxel, center=(0.0, 0.0, 0.0)):
 
 
 def phantom_volume(blobs: Sequence[Blob], shape_zyx, voxel, center=(0.0, 0.0, 0.0),
-                   supersample: int = 2) -> np.ndarray:
-    """Ground-truth density on the voxel grid [Z,Y,X] (FP64).
+                   supersample: int = 2, device=None):
+    """Ground-truth density on the voxel grid [Z,Y,X].
 
     Ellipsoids are averaged over supersample^3 sub-voxel points; Gaussian
-    blobs are evaluated at the voxel centres.
+    blobs are evaluated at the voxel centres.  device=None: FP64 numpy;
+    otherwise an FP32 torch tensor evaluated (in FP32) on that device.
     """
+    if device is not None:
+        return _phantom_volume_torch(blobs, shape_zyx, voxel, center, supersample, device)
     nz, ny, nx = shape_zyx
     out = np.zeros((nz, ny, nx))
     xs, ys, zs = voxel_centers(shape_zyx, voxel, center)
@@ -336,6 +339,31 @@ def phantom_volume(blobs: Sequence[Blob], shape_zyx, voxel, center=(0.0, 0.0, 0.
                     q = np.einsum("ij,zyxj->zyxi", T, pts)
                     acc += (np.sum(q * q, -1) <= 1.0)
         out += b.rho * acc / ss ** 3
+    return out
+
+
+def _phantom_volume_torch(blobs, shape_zyx, voxel, center, ss, device):
+    t = torch
+    nz, ny, nx = shape_zyx
+    xs, ys, zs = (t.as_tensor(a, dtype=t.float32, device=device)
+                  for a in voxel_centers(shape_zyx, voxel, center))
+    out = t.zeros((nz, ny, nx), dtype=t.float32, device=device)
+    offs = [((k + 0.5) / ss - 0.5) for k in range(ss)]
+    for b in blobs:
+        T = t.as_tensor((b.rot / b.axes[None, :]).T, dtype=t.float32, device=device)
+        c = t.as_tensor(b.center, dtype=t.float32, device=device)
+        pts = [(0.0, 0.0, 0.0)] if b.kind == "gauss" else \
+              [(ox, oy, oz) for oz in offs for oy in offs for ox in offs]
+        acc = t.zeros_like(out)
+        for (ox, oy, oz) in pts:
+            X = (xs + ox * voxel[0] - c[0])[None, None, :]
+            Y = (ys + oy * voxel[1] - c[1])[None, :, None]
+            Z = (zs + oz * voxel[2] - c[2])[:, None, None]
+            q = (T[0, 0] * X + T[0, 1] * Y + T[0, 2] * Z) ** 2 \
+                + (T[1, 0] * X + T[1, 1] * Y + T[1, 2] * Z) ** 2 \
+                + (T[2, 0] * X + T[2, 1] * Y + T[2, 2] * Z) ** 2
+            acc += t.exp(-0.5 * q) if b.kind == "gauss" else (q <= 1.0).float()
+        out += b.rho * acc / len(pts)
     return out
 
 
@@ -421,6 +449,39 @@ def workload(name: str) -> Workload:
         return Workload(name, o, 480, 620, 0.616, 360, 785, 0.616, (128, 512, 512),
                         (0.25, 0.25, 0.25), seed=7, n_objects=20)
     raise KeyError(name)
+
+
+def batch_workloads(n: int = 12, seed: int = 100, max_views: int = 720,
+                    max_det=(480, 616), sizes=(128, 192, 256, 384, 512),
+                    min_views: int = 200, min_det: int = 256) -> List[Workload]:
+    """Uneven problems for the batched launch: kinds cycle circle, sinusoid,
+    circle plus arc; problem k uses seed + k for view count
+    U{min_views..max_views}, detector W x H between min_det^2 and max_det
+    (multiples of 8, same
+    physical width as the 512-column preset), and a cubic volume from `sizes`
+    over the same 192 mm field."""
+    out = []
+    kinds = ["circle", "sinusoid", "circle_arc"]
+    for k in range(n):
+        rng = np.random.default_rng(seed + k)
+        kind = kinds[k % 3]
+        V = int(rng.integers(min_views, max_views + 1))
+        Wd = int(rng.integers(min_det // 8, max_det[1] // 8 + 1)) * 8
+        Hd = int(rng.integers(min_det // 8, min(max_det[0], Wd) // 8 + 1)) * 8
+        N = int(rng.choice(sizes))
+        pitch = 0.6 * 512 / Wd
+        if kind == "circle":
+            o = circle_orbit(V)
+        elif kind == "sinusoid":
+            o = sinusoid_orbit(V)
+        else:
+            nc = max(2, int(round(V * 360 / 496)))
+            o = circle_arc_orbit(nc, max(2, V - nc))
+        n_mu = 360 if Wd <= 384 else 720
+        vox = 192.0 / N
+        out.append(Workload(f"batch{k}_{kind}", o, Hd, Wd, pitch, n_mu, Wd, pitch, (N, N, N),
+                            (vox, vox, vox), seed=seed + k, n_objects=20))
+    return out
 
 
 def scaled_workload(name: str, views: Optional[int] = None, det=None, vol=None,
