@@ -132,6 +132,26 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+KERNEL_SOURCES = {"k_bp3d": "paper_2410_14900_gb300/csrc/dc_backproject.cu",
+                  "k_linesum": "paper_2410_14900_gb300/csrc/dc_filter.cu",
+                  "k_bp2d": "paper_2410_14900_gb300/csrc/dc_filter.cu"}
+
+
+def recorded_traffic(kernel: str, per_launch_units: float):
+    """DRAM bytes per launch from the ncu capture recorded in
+    profiles/traffic.json, scaled to this launch's work units; None when no
+    capture exists or the kernel's source changed since it was taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        src = open(os.path.join(ROOT, KERNEL_SOURCES[kernel]), "rb").read()
+    except Exception:
+        return None
+    if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
+        return None
+    return rec["dram_bytes_per_launch"] * per_launch_units / rec["units_per_launch"]
+
+
 def work_units(desc, B):
     """Algorithmic units per step: Joseph steps, pixel-angle pairs, updates."""
     V, H, W = desc["n_views"], desc["det_rows"], desc["det_cols"]
@@ -319,8 +339,9 @@ def run_ours(args, rank, world, local_rank):
     w = synth.workload(args.workload)
     desc = w.desc_dict()
     geom = api.Geometry(desc, w.matrices(), w.orbit.vdl)
-    # every rank reconstructs its own seeded phantom
-    blobs = synth.random_ellipsoids(np.random.default_rng(w.seed + 1000 * rank),
+    # every rank reconstructs its own seeded phantom (independent problems)
+    from paper_2410_14900_gb300 import sharding
+    blobs = synth.random_ellipsoids(np.random.default_rng(sharding.rank_seed(w.seed, rank)),
                                     w.n_objects, w.r_fov())
     g = synth.project_phantom(blobs, w.orbit, w.det_rows, w.det_cols, w.pitch,
                               device=dev, dtype=torch.float32)[None].contiguous()
@@ -371,10 +392,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize()
     ms_step = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = sharding.max_over_ranks(ms_step, dist if world > 1 else None, dev)
     api.dc_sync_status(geom)
 
     kernels = {}
@@ -393,7 +411,8 @@ def run_ours(args, rank, world, local_rank):
         per_launch_units = units[dom] * args.steps / kernels[dom]["launches"]
         ach = per_launch_units * FLOPS_PER_UNIT[dom] / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops,
+                "traffic": recorded_traffic(dom, per_launch_units),
                 "peak_source": f"FP32 issue rate: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x "
                                f"2 x {sm_max:.0f} MHz (max clock of {peak_kind} peaks)",
                 "units_per_launch": per_launch_units,
@@ -435,10 +454,7 @@ def run_ours(args, rank, world, local_rank):
         a1.record(stream)
         torch.cuda.synchronize()
         t_e2e = a0.elapsed_time(a1) / args.steps
-        if world > 1:
-            t = torch.tensor([t_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = sharding.max_over_ranks(t_e2e, dist if world > 1 else None, dev)
         e2e = {"value": t_e2e / (B * world), "unit": UNIT,
                "h2d_bytes_per_step": int(g.numel() * 4), "d2h_bytes_per_step": int(vol.numel() * 4)}
 
@@ -484,7 +500,8 @@ def run_ours(args, rank, world, local_rank):
         cpu = {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": ms_step / (B * world), "unit": UNIT, "n_gpus": world,
+        line = {"metric": METRIC, "value": sharding.whole_job_ms_per_volume(ms_step, B, world),
+                "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic: seeded 20-ellipsoid phantom, exact line integrals",
