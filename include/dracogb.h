@@ -68,6 +68,9 @@ extern "C" {
 #define DC_KAHAN 2u           /* compensated (Kahan) summation over views   */
 #define DC_RELU 4u            /* ReLU after the sum over views (Sec. 2.3)   */
 
+/* maximum number of orbit segments of dc_crofton_weights */
+#define DC_MAX_SEGMENTS 16
+
 /* doubles per view returned by dc_get_view_geometry */
 #define DC_VIEW_GEO_N 24
 
@@ -183,6 +186,27 @@ int dc_backproject(const dc_geometry *geom, int B, const void *gF, int dtype,
  */
 int dc_backproject_adjoint(const dc_geometry *geom, int B, const float *grad_vol,
                            const float *relu_vol, float *grad_gF, void *stream);
+
+/*
+ * dc_crofton_weights -- the smooth Crofton weights of Eq. 9 as redundancy
+ * weights W for dc_filter (the analytic alternative to learned weights):
+ *   M(theta, lambda_i) = |v_i.theta|^m c_i / sum_alpha |v_alpha.theta|^m c_alpha
+ * for every view i and plane (mu_m, s_{k+1/2}) through the source.  The
+ * intersections alpha of the plane with the orbit are view i and each sign
+ * change of (a_j - a_i).theta between consecutive views of a segment (tangent
+ * and c interpolated linearly at the crossing).  c = 1 except within `taper`
+ * views of the ends of an open segment (c = sin^2(pi/2 (d + 1/2)/taper) at
+ * distance d from the end).
+ *   n_seg, seg_start, seg_closed: host arrays describing the orbit's pieces,
+ *     view ranges [seg_start[q], seg_start[q+1]) with seg_start[0] = 0; n_seg
+ *     = 0 means one piece, closed as the descriptor says.
+ *   m: 0..8 (m = 0 gives 1/n, the Crofton symbol itself).
+ *   W: device, [V][n_mu][n_s] FP32, written (entry n_s-1 = 0; 0 where
+ *     v_i.theta = 0).
+ * A full circle gives 1/2 wherever the plane is not tangent to the orbit.
+ */
+int dc_crofton_weights(const dc_geometry *geom, int n_seg, const int *seg_start,
+                       const int *seg_closed, int m, int taper, float *W, void *stream);
 
 /*
  * Batched reconstruction of several problems (orbits with uneven view

@@ -581,3 +581,88 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Smooth Crofton weight of Eq. 9                                            */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * M(theta, lambda_i) = |v_i.theta|^m c_i / sum_alpha |v_alpha.theta|^m c_alpha
+ * for every view i and plane (mu, s_{k+1/2}) through a_i.  The sum runs over
+ * the intersections of that plane with the orbit: view i itself, and every
+ * sign change of f_j = (a_j - a_i).theta between consecutive views j, j+1 of
+ * a segment (wrapping for a closed segment; pairs that contain i are skipped
+ * because the crossing at i is counted by the first term).  At a crossing
+ * t = f_j / (f_j - f_{j+1}) interpolates the tangent v and the taper c.
+ * c is 1 except within `taper` views of the ends of an open segment, where
+ * c = sin^2(pi/2 (d + 1/2) / taper) at distance d from the end.  Segments:
+ * view ranges [seg_start[q], seg_start[q+1]) (the last ends at V) with
+ * seg_closed[q].  out[V][n_mu][n_s]; entry n_s-1 is 0; M = 0 where
+ * |v_i.theta| = 0.
+ */
+static double crofton_taper(int j, int lo, int hi, int closed, int taper) {
+  if (closed || taper <= 0) return 1.0;
+  int d = j - lo < hi - 1 - j ? j - lo : hi - 1 - j;
+  if (d >= taper) return 1.0;
+  double x = sin(0.5 * PI * (d + 0.5) / taper);
+  return x * x;
+}
+
+void orc_crofton_weights(int V, int n_mu, int n_s, double ds, const double *geo,
+                         int n_seg, const int *seg_start, const int *seg_closed, int m,
+                         int taper, double *out) {
+  double *cj = malloc(sizeof(double) * V);
+  int *segof = malloc(sizeof(int) * V);
+  for (int q = 0; q < n_seg; ++q) {
+    int lo = seg_start[q], hi = q + 1 < n_seg ? seg_start[q + 1] : V;
+    for (int j = lo; j < hi; ++j) {
+      cj[j] = crofton_taper(j, lo, hi, seg_closed[q], taper);
+      segof[j] = q;
+    }
+  }
+#pragma omp parallel for schedule(dynamic) collapse(2)
+  for (int i = 0; i < V; ++i)
+    for (int mm = 0; mm < n_mu; ++mm) {
+      const double *gi = geo + (size_t)GEO_N * i;
+      double D = gi[G_D];
+      const double *lx = gi + G_LX, *ly = gi + G_LY, *lz = gi + G_LZ, *ai = gi + G_A;
+      double mu = mm * PI / n_mu, cm = cos(mu), sm = sin(mu);
+      for (int k = 0; k < n_s; ++k) {
+        double *o = out + ((size_t)i * n_mu + mm) * n_s + k;
+        if (k == n_s - 1) {
+          *o = 0.0;
+          continue;
+        }
+        double sh = s_of(k, n_s, ds) + 0.5 * ds;
+        double nrm = sqrt(D * D + sh * sh), th[3];
+        for (int t = 0; t < 3; ++t) th[t] = (D * cm * lx[t] + D * sm * ly[t] + sh * lz[t]) / nrm;
+        double own = pow(fabs(dot3(gi + G_V, th)), m) * cj[i];
+        if (!(own > 0.0)) {
+          *o = 0.0;
+          continue;
+        }
+        double sum = own;
+        for (int q = 0; q < n_seg; ++q) {
+          int lo = seg_start[q], hi = q + 1 < n_seg ? seg_start[q + 1] : V;
+          int npair = seg_closed[q] ? hi - lo : hi - lo - 1;
+          for (int e = 0; e < npair; ++e) {
+            int j0 = lo + e, j1 = (j0 + 1 < hi) ? j0 + 1 : lo;
+            if (j0 == i || j1 == i) continue;
+            const double *a0 = geo + (size_t)GEO_N * j0 + G_A, *a1 = geo + (size_t)GEO_N * j1 + G_A;
+            double f0 = (a0[0] - ai[0]) * th[0] + (a0[1] - ai[1]) * th[1] + (a0[2] - ai[2]) * th[2];
+            double f1 = (a1[0] - ai[0]) * th[0] + (a1[1] - ai[1]) * th[1] + (a1[2] - ai[2]) * th[2];
+            if ((f0 < 0.0) == (f1 < 0.0)) continue;
+            double t = f0 / (f0 - f1), va[3];
+            const double *v0 = geo + (size_t)GEO_N * j0 + G_V, *v1 = geo + (size_t)GEO_N * j1 + G_V;
+            for (int c = 0; c < 3; ++c) va[c] = (1.0 - t) * v0[c] + t * v1[c];
+            double ca = (1.0 - t) * cj[j0] + t * cj[j1];
+            sum += pow(fabs(dot3(va, th)), m) * ca;
+          }
+        }
+        *o = own / sum;
+      }
+    }
+  (void)segof;
+  free(cj);
+  free(segof);
+}

@@ -300,6 +300,26 @@ def backproject_adjoint(geom: Geometry, grad_vol: np.ndarray) -> np.ndarray:
     return out
 
 
+def crofton_weights(geom: Geometry, segments=None, m: int = 2, taper: int = 5) -> np.ndarray:
+    """Smooth Crofton weights of Eq. 9 for every (view, mu, s_{k+1/2}).
+
+    segments: list of (first_view, closed) for the orbit's pieces (default:
+    one piece, closed as the descriptor says).
+    """
+    d = geom.desc
+    V = d["n_views"]
+    if segments is None:
+        segments = [(0, bool(d.get("closed_orbit", 1)))]
+    st = np.ascontiguousarray([s[0] for s in segments], dtype=np.int32)
+    cl = np.ascontiguousarray([int(bool(s[1])) for s in segments], dtype=np.int32)
+    out = np.empty((V, d["n_mu"], d["n_s"]))
+    IP = ctypes.POINTER(ctypes.c_int)
+    lib().orc_crofton_weights(_ci(V), _ci(d["n_mu"]), _ci(d["n_s"]), _cd(d["ds"]), _p(geom.geo),
+                              _ci(len(segments)), st.ctypes.data_as(IP), cl.ctypes.data_as(IP),
+                              _ci(m), _ci(taper), _p(out))
+    return out
+
+
 def reconstruct(geom: Geometry, g: np.ndarray, Wred=None, relu=False) -> np.ndarray:
     """Eq. 12: f = A3d^T w_d A2d^T D w_red w_sino D A2d w_cos g."""
     return backproject(geom, filter(geom, g, Wred), relu=relu)

@@ -52,6 +52,8 @@ _SIGS = {
     "dc_radon2d": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "dc_radon2d_adjoint": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "dc_sync_status": (ctypes.c_int, [_P, _P]),
+    "dc_crofton_weights": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int,
+                                          _P, _P]),
     "dc_batch_create": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int, ctypes.c_uint,
                                        ctypes.POINTER(ctypes.c_void_p)]),
     "dc_batch_run": (ctypes.c_int, [_P, _P, _P, _P, _P]),

@@ -231,6 +231,25 @@ def dc_radon2d_adjoint(geom: Geometry, R: torch.Tensor) -> torch.Tensor:
     return img
 
 
+def dc_crofton_weights(geom: Geometry, segments=None, m: int = 2, taper: int = 5) -> torch.Tensor:
+    """Smooth Crofton weights of Eq. 9, [V, n_mu, n_s], usable as W.
+
+    segments: list of (first_view, closed) pieces of the orbit (None: one
+    piece, closed as the descriptor says).
+    """
+    W = torch.empty((geom.V,) + geom.sino_shape, device="cuda", dtype=torch.float32)
+    if segments:
+        st = (ctypes.c_int * len(segments))(*[int(s[0]) for s in segments])
+        cl = (ctypes.c_int * len(segments))(*[int(bool(s[1])) for s in segments])
+        n = len(segments)
+    else:
+        st = cl = None
+        n = 0
+    check(_lib.load().dc_crofton_weights(geom.handle, n, st, cl, int(m), int(taper), _ptr(W),
+                                         _stream()), "dc_crofton_weights")
+    return W
+
+
 def dc_sync_status(geom: Geometry):
     """Wait for the current stream; raise if a device-side wait timed out."""
     check(_lib.load().dc_sync_status(geom.handle, _stream()), "dc_sync_status")

@@ -376,11 +376,26 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
         // raw box -> FP32 pair tile (times the FP16 scale)
         const T *raw = (const T *)(dsm + s * STAGE_BYTES);
         const int bw = t.w;
-        for (int e = tid; e < TB_BH * bw; e += TB_TX * TB_TY) {
-          int r = e / bw, j = e - r * bw;
-          float g0 = sld(raw + e) * sc;
-          float g1 = (j + 1 < bw) ? sld(raw + e + 1) * sc : 0.0f;
-          wt[r * TB_S2 + j] = make_float2(g0, g1);
+        if (sizeof(T) == 4) {
+          // four pairs per thread and step: one 16-byte load (+ the next
+          // element) and two 16-byte stores
+          const int lg = (bw == TB_BWN) ? 3 : 4;  // log2 of the groups per row
+          for (int e = tid; e < (TB_BH * bw) >> 2; e += TB_TX * TB_TY) {
+            int r = e >> lg, j4 = (e - (r << lg)) << 2;
+            const float *src = (const float *)raw + r * bw + j4;
+            float4 v = *(const float4 *)src;
+            float nx = (j4 + 4 < bw) ? src[4] : 0.0f;
+            float4 *dst = (float4 *)(wt + r * TB_S2 + j4);
+            dst[0] = make_float4(v.x, v.y, v.y, v.z);
+            dst[1] = make_float4(v.z, v.w, v.w, nx);
+          }
+        } else {
+          for (int e = tid; e < TB_BH * bw; e += TB_TX * TB_TY) {
+            int r = e / bw, j = e - r * bw;
+            float g0 = sld(raw + e) * sc;
+            float g1 = (j + 1 < bw) ? sld(raw + e + 1) * sc : 0.0f;
+            wt[r * TB_S2 + j] = make_float2(g0, g1);
+          }
         }
       }
       if (__syncthreads_or(!w_ok)) {
@@ -405,48 +420,105 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
           int j = dc::floor_frac(u, fu);
           const float2 *col = wt + j;
           float vb = fmaf(V0, rw, cvl), dv = dV * rw;
+          // v is affine in k: the column stays inside the tile if both ends do
+          float vlast = fmaf((float)(NZ - 1), dv, vb);
+          if (fminf(vb, vlast) >= 0.01f && fmaxf(vb, vlast) <= vmx - 0.01f) {
 #pragma unroll
-          for (int k = 0; k < NZ; ++k) {
-            float kf = (float)k;
-            float v = fminf(fmaxf(fmaf(kf, dv, vb), 0.0f), vmx), fv;
-            int r = dc::floor_frac(v, fv);
-            const float2 *p = col + r * TB_S2;
-            float2 q0 = p[0], q1 = p[TB_S2];
-            float x0 = fmaf(fu, q0.y - q0.x, q0.x), x1 = fmaf(fu, q1.y - q1.x, q1.x);
-            float val = fmaf(fv, x1 - x0, x0);
-            float ez = fmaf(kf, a.dz, ez0);
-            float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
-            if (KAHAN) {
-              float y = term - cmp[k];
-              float tt = acc[k] + y;
-              cmp[k] = (tt - acc[k]) - y;
-              acc[k] = tt;
-            } else {
-              acc[k] += term;
+            for (int k = 0; k < NZ; ++k) {
+              float kf = (float)k, fv;
+              int r = dc::floor_frac(fmaf(kf, dv, vb), fv);
+              const float2 *p = col + r * TB_S2;
+              float2 q0 = p[0], q1 = p[TB_S2];
+              float x0 = fmaf(fu, q0.y - q0.x, q0.x), x1 = fmaf(fu, q1.y - q1.x, q1.x);
+              float val = fmaf(fv, x1 - x0, x0);
+              float ez = fmaf(kf, a.dz, ez0);
+              float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
+              if (KAHAN) {
+                float y = term - cmp[k];
+                float tt = acc[k] + y;
+                cmp[k] = (tt - acc[k]) - y;
+                acc[k] = tt;
+              } else {
+                acc[k] += term;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < NZ; ++k) {
+              float kf = (float)k;
+              float v = fminf(fmaxf(fmaf(kf, dv, vb), 0.0f), vmx), fv;
+              int r = dc::floor_frac(v, fv);
+              const float2 *p = col + r * TB_S2;
+              float2 q0 = p[0], q1 = p[TB_S2];
+              float x0 = fmaf(fu, q0.y - q0.x, q0.x), x1 = fmaf(fu, q1.y - q1.x, q1.x);
+              float val = fmaf(fv, x1 - x0, x0);
+              float ez = fmaf(kf, a.dz, ez0);
+              float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
+              if (KAHAN) {
+                float y = term - cmp[k];
+                float tt = acc[k] + y;
+                cmp[k] = (tt - acc[k]) - y;
+                acc[k] = tt;
+              } else {
+                acc[k] += term;
+              }
             }
           }
         } else {
+          // (u, v) = (affine in k) / (affine depth > 0): monotonic in k, so
+          // the column stays inside the tile if both end voxels do
+          float kl = (float)(NZ - 1);
+          float rwl = dc::rcp_approx(fmaf(kl, dW, W0)), rw0 = dc::rcp_approx(W0);
+          float u0 = fmaf(U0, rw0, cul), ul = fmaf(fmaf(kl, dU, U0), rwl, cul);
+          float v0 = fmaf(V0, rw0, cvl), vl = fmaf(fmaf(kl, dV, V0), rwl, cvl);
+          const float m = 0.01f;  // margin for the rounding of the end points
+          if (fminf(u0, ul) >= m && fmaxf(u0, ul) <= umx - m && fminf(v0, vl) >= m &&
+              fmaxf(v0, vl) <= vmx - m) {
 #pragma unroll
-          for (int k = 0; k < NZ; ++k) {
-            float kf = (float)k;
-            float rw = dc::rcp_approx(fmaf(kf, dW, W0));
-            float u = fminf(fmaxf(fmaf(fmaf(kf, dU, U0), rw, cul), 0.0f), umx);
-            float v = fminf(fmaxf(fmaf(fmaf(kf, dV, V0), rw, cvl), 0.0f), vmx);
-            float fu, fv;
-            int j = dc::floor_frac(u, fu), r = dc::floor_frac(v, fv);
-            const float2 *p = wt + r * TB_S2 + j;
-            float2 q0 = p[0], q1 = p[TB_S2];
-            float x0 = fmaf(fu, q0.y - q0.x, q0.x), x1 = fmaf(fu, q1.y - q1.x, q1.x);
-            float val = fmaf(fv, x1 - x0, x0);
-            float ez = fmaf(kf, a.dz, ez0);
-            float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
-            if (KAHAN) {
-              float y = term - cmp[k];
-              float tt = acc[k] + y;
-              cmp[k] = (tt - acc[k]) - y;
-              acc[k] = tt;
-            } else {
-              acc[k] += term;
+            for (int k = 0; k < NZ; ++k) {
+              float kf = (float)k;
+              float rw = dc::rcp_approx(fmaf(kf, dW, W0));
+              float fu, fv;
+              int j = dc::floor_frac(fmaf(fmaf(kf, dU, U0), rw, cul), fu);
+              int r = dc::floor_frac(fmaf(fmaf(kf, dV, V0), rw, cvl), fv);
+              const float2 *p = wt + r * TB_S2 + j;
+              float2 q0 = p[0], q1 = p[TB_S2];
+              float x0 = fmaf(fu, q0.y - q0.x, q0.x), x1 = fmaf(fu, q1.y - q1.x, q1.x);
+              float val = fmaf(fv, x1 - x0, x0);
+              float ez = fmaf(kf, a.dz, ez0);
+              float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
+              if (KAHAN) {
+                float y = term - cmp[k];
+                float tt = acc[k] + y;
+                cmp[k] = (tt - acc[k]) - y;
+                acc[k] = tt;
+              } else {
+                acc[k] += term;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < NZ; ++k) {
+              float kf = (float)k;
+              float rw = dc::rcp_approx(fmaf(kf, dW, W0));
+              float u = fminf(fmaxf(fmaf(fmaf(kf, dU, U0), rw, cul), 0.0f), umx);
+              float v = fminf(fmaxf(fmaf(fmaf(kf, dV, V0), rw, cvl), 0.0f), vmx);
+              float fu, fv;
+              int j = dc::floor_frac(u, fu), r = dc::floor_frac(v, fv);
+              const float2 *p = wt + r * TB_S2 + j;
+              float2 q0 = p[0], q1 = p[TB_S2];
+              float x0 = fmaf(fu, q0.y - q0.x, q0.x), x1 = fmaf(fu, q1.y - q1.x, q1.x);
+              float val = fmaf(fv, x1 - x0, x0);
+              float ez = fmaf(kf, a.dz, ez0);
+              float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
+              if (KAHAN) {
+                float y = term - cmp[k];
+                float tt = acc[k] + y;
+                cmp[k] = (tt - acc[k]) - y;
+                acc[k] = tt;
+              } else {
+                acc[k] += term;
+              }
             }
           }
         }
@@ -582,7 +654,8 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_batched(const BatchPro
 // voxel's distance is at least d_min.  That bound maps to 2^30, so the sums
 // cannot overflow; each contribution is rounded to the nearest unit.
 constexpr int TA_S = TB_BWW + 1;
-static_assert(TB_BWW == 64, "the tile flush indexes columns with a 6-bit shift");
+static_assert(TB_BWW == 64 && TB_BWN == 32,
+              "the tile flush and the pair copy index columns with shifts");
 
 __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) {
   __shared__ int tile[TB_BH * TA_S];

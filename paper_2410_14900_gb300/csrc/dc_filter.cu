@@ -424,7 +424,8 @@ struct BP2Args {
 };
 
 struct BPMu {
-  float F00, I00, Bc, Bs, winv, pad0, pad1, pad2;
+  float F00, I00, Bc, Bs, winv, pad0, pad1;
+  int i00;  // I00 as an integer
 };
 
 __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
@@ -489,7 +490,8 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
       float xmax = M.F00 + fmaxf(ex, 0.0f) + fmaxf(ey, 0.0f);
       M.pad0 = (xmin >= -1.0f - M.I00 + 0.01f && xmax <= (float)a.n_s - M.I00 - 0.01f) ? 1.0f
                                                                                           : 0.0f;
-      M.pad1 = M.pad2 = 0.0f;
+      M.pad1 = 0.0f;
+      M.i00 = (int)M.I00;
       bmu[c & 1][mi] = M;
     }
   };
@@ -505,6 +507,11 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
 #pragma unroll
     for (int q = 0; q < BP2_NQ; ++q) acc[ry][q] = 0.0f;
   const float rl0 = (float)(warp * BP2_RY);
+  float jlf[BP2_NQ], rlf[BP2_RY];  // pixel offsets inside the tile, as floats
+#pragma unroll
+  for (int q = 0; q < BP2_NQ; ++q) jlf[q] = (float)(lane + 32 * q);
+#pragma unroll
+  for (int ry = 0; ry < BP2_RY; ++ry) rlf[ry] = rl0 + (float)ry;
 
   bool ok = true;
   for (int c = 0; c < nchunk; ++c) {
@@ -518,16 +525,16 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
     int nm = min(BP2_MC, a.n_mu - c * BP2_MC);
     for (int mi = 0; mi < nm; ++mi) {
       const BPMu M = bmu[c & 1][mi];
-      const float *row = st + mi * rstride + PADL + (int)M.I00;
+      const float *row = st + mi * rstride + PADL + M.i00;
       float w1c = 1.0f - M.winv;
       if (M.pad0 != 0.0f) {
 #pragma unroll
         for (int ry = 0; ry < BP2_RY; ++ry) {
-          float rt = fmaf(rl0 + (float)ry, M.Bs, M.F00);
+          float rt = fmaf(rlf[ry], M.Bs, M.F00);
 #pragma unroll
           for (int q = 0; q < BP2_NQ; ++q) {
             float f;
-            int k = dc::floor_frac(fmaf((float)(lane + 32 * q), M.Bc, rt), f);
+            int k = dc::floor_frac(fmaf(jlf[q], M.Bc, rt), f);
             const float *p = row + k;
             float w0 = fmaxf(0.0f, fmaf(-f, M.winv, 1.0f));
             float w1 = fmaxf(0.0f, fmaf(f, M.winv, w1c));
@@ -538,10 +545,10 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
         float lo = -1.0f - M.I00, hi = (float)a.n_s - M.I00;
 #pragma unroll
         for (int ry = 0; ry < BP2_RY; ++ry) {
-          float rt = fmaf(rl0 + (float)ry, M.Bs, M.F00);
+          float rt = fmaf(rlf[ry], M.Bs, M.F00);
 #pragma unroll
           for (int q = 0; q < BP2_NQ; ++q) {
-            float xi = fminf(fmaxf(fmaf((float)(lane + 32 * q), M.Bc, rt), lo), hi);
+            float xi = fminf(fmaxf(fmaf(jlf[q], M.Bc, rt), lo), hi);
             float f;
             int k = dc::floor_frac(xi, f);
             const float *p = row + k;
@@ -814,8 +821,8 @@ int alloc_workspace(dc_geometry *g) {
   g->imgT_stride = (size_t)d.det_cols * g->Hp;
   g->sino_stride = (size_t)d.n_mu * g->NSp;
   size_t per_img = (g->img_stride + g->imgT_stride + 2 * g->sino_stride) * sizeof(float);
-  // keep one chunk's work area near 48 MB so that it stays resident in L2
-  long target = 48L << 20;
+  // keep one chunk's work area near 80 MB so that it stays resident in L2
+  long target = 80L << 20;
   const char *env = getenv("DC_CHUNK_IMAGES");
   int ci = env ? atoi(env) : (int)(target / (long)per_img);
   if (ci < 4) ci = 4;

@@ -482,3 +482,106 @@ def test_mse_gradient_matches_central_differences():
         e[idx] = h
         fd = (loss(g + e, Wr) - loss(g - e, Wr)) / (2 * h)
         assert abs(fd - gg[idx]) <= 1e-8 * max(1.0, abs(fd))
+
+
+# ------------------------------------------------------ Crofton weights (Eq. 9)
+def test_crofton_weights_are_one_half_on_a_circle():
+    """Every plane through a circle point meets the circle once more, with the
+    same |a'.theta| by symmetry: M = 1/2 (Eq. 14).  Planes tangent to the
+    orbit at the source (K ~ 0) carry no weight and are excluded."""
+    o, d, P = _small_circle(V=48, H=40, W=40, p=3.0, n_mu=24, n_s=40)
+    geom = orc.Geometry(d, P, o.vdl)
+    M = orc.crofton_weights(geom, m=2)[:, :, :-1]
+    K = np.stack([orc.redundancy_K(geom, i) for i in range(d["n_views"])])[:, :, :-1]
+    use = np.abs(K) > 0.01 * np.abs(K).max()
+    assert use.mean() > 0.9
+    # the crossing's tangent is interpolated linearly between views
+    assert np.abs(M[use] - 0.5).max() < 5e-3
+
+
+def _arc_crossings(o, i, th, n_circle):
+    """Independent count of the plane's intersections with a circle+arc orbit
+    (the circle in z = 0, the arc in the x-z plane), excluding view i."""
+    ai = o.sources[i]
+    R = np.linalg.norm(o.sources[0])
+    c = th @ ai
+    rxy = math.hypot(th[0], th[1])
+    n_circ = 0
+    if rxy > 0:
+        dist = abs(c) / rxy
+        if abs(dist - R) < 1e-3 * R:
+            return None           # near tangency: count not robust
+        n_circ = 2 if dist < R else 0
+    psi = np.linspace(-math.pi / 6, math.pi / 6, 20001)
+    f = (R * np.cos(psi)) * th[0] + (R * np.sin(psi)) * th[2] - c
+    psi_i = math.atan2(ai[2], ai[0])
+    sgn = np.sign(f)
+    idx = np.nonzero(sgn[:-1] * sgn[1:] < 0)[0]
+    roots = psi[idx]
+    # drop the root at the source itself; reject roots near the arc ends
+    roots = roots[np.abs(roots - psi_i) > 2e-3]
+    if np.any(np.abs(np.abs(roots) - math.pi / 6) < 0.05):
+        return None
+    if i < n_circle:
+        # source on the circle: the circle's second crossing, arc crossings
+        return (n_circ - 1 if n_circ else 0) + len(roots)
+    return n_circ + len(roots)
+
+
+def test_crofton_m0_is_the_crofton_symbol_on_circle_plus_arc():
+    """m = 0, no taper: M = 1/n with n the number of intersections of the plane
+    with the orbit (Eq. 3's Crofton symbol), counted independently."""
+    nc, na = 60, 21
+    o = synth.circle_arc_orbit(nc, na)
+    H = W = 48
+    p = 2.5
+    P = synth.projection_matrices(o, H, W, p)
+    d = dict(n_views=o.n_views, det_rows=H, det_cols=W, n_mu=16, n_s=48, pitch=p, ds=p,
+             closed_orbit=0)
+    geom = orc.Geometry(d, P, o.vdl)
+    M = orc.crofton_weights(geom, [(0, True), (nc, False)], m=0, taper=0)
+    checked = 0
+    for i in (3, 25, nc + 4, nc + 10, nc + 17):
+        lx, ly, lz = o.lx[i], o.ly[i], o.lz[i]
+        for m_ in range(16):
+            mu = m_ * math.pi / 16
+            for k in range(0, 47, 3):
+                s = (k - 23.5 + 0.5) * p
+                th = (o.sdd * math.cos(mu) * lx + o.sdd * math.sin(mu) * ly + s * lz)
+                th = th / np.linalg.norm(th)
+                if abs(o.vdl[i] @ th) < 1e-3 * np.linalg.norm(o.vdl[i]):
+                    continue
+                n_other = _arc_crossings(o, i, th, nc)
+                if n_other is None:
+                    continue
+                assert abs(M[i, m_, k] - 1.0 / (1 + n_other)) < 1e-12, (i, m_, k, n_other)
+                checked += 1
+    assert checked > 200
+
+
+def test_crofton_weights_reconstruct_circle_plus_arc_off_midplane():
+    """A circle plus arc satisfies Tuy's condition: with the Eq. 9 weights the
+    reconstruction of blobs away from the circle's plane is accurate, where
+    the circle's weight 1/2 leaves large cone-beam errors."""
+    nc, na, n, p, nmu, N = 72, 30, 72, 1.6, 90, 30
+    o = synth.circle_arc_orbit(nc, na)
+    vox = 60.0 / N
+    d = dict(n_views=o.n_views, det_rows=n, det_cols=n, n_mu=nmu, n_s=n, pitch=p, ds=p,
+             vol_x=N, vol_y=N, vol_z=N, voxel=(vox, vox, vox), closed_orbit=0)
+    geom = orc.Geometry(d, synth.projection_matrices(o, n, n, p), o.vdl)
+    blobs = [synth.Blob("gauss", np.array([0.0, 0.0, 14.0]), np.array([5.0, 5.0, 5.0]),
+                        np.eye(3), 1.0),
+             synth.Blob("gauss", np.array([8.0, -6.0, -10.0]), np.array([3.0, 4.0, 3.5]),
+                        np.eye(3), 0.6)]
+    g = synth.project_phantom(blobs, o, n, n, p)
+    gt = synth.phantom_volume(blobs, (N, N, N), (vox, vox, vox))
+    c = (np.arange(N) - (N - 1) / 2) * vox
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    roi = (X ** 2 + Y ** 2 + Z ** 2) < 26 ** 2
+    M = orc.crofton_weights(geom, [(0, True), (nc, False)], m=2, taper=3)
+    err = {}
+    for name, Wt in (("half", None), ("crofton", M)):
+        f = orc.reconstruct(geom, g[None], Wt)[0]
+        err[name] = np.linalg.norm((f - gt)[roi]) / np.linalg.norm(gt[roi])
+    assert err["crofton"] < 0.04, err
+    assert err["half"] > 4 * err["crofton"], err
