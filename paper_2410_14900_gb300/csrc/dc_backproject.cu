@@ -390,11 +390,21 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
             dst[1] = make_float4(v.z, v.w, v.w, nx);
           }
         } else {
-          for (int e = tid; e < TB_BH * bw; e += TB_TX * TB_TY) {
-            int r = e / bw, j = e - r * bw;
-            float g0 = sld(raw + e) * sc;
-            float g1 = (j + 1 < bw) ? sld(raw + e + 1) * sc : 0.0f;
-            wt[r * TB_S2 + j] = make_float2(g0, g1);
+          // 16-bit storage: four values per 8-byte load, converted (and
+          // scaled) to FP32 pairs with two 16-byte stores
+          const int lg = (bw == TB_BWN) ? 3 : 4;
+          for (int e = tid; e < (TB_BH * bw) >> 2; e += TB_TX * TB_TY) {
+            int r = e >> lg, j4 = (e - (r << lg)) << 2;
+            const T *src = raw + r * bw + j4;
+            uint2 pk = *(const uint2 *)src;
+            T h[4];
+            memcpy(h, &pk, sizeof(pk));
+            float v0 = sld(&h[0]) * sc, v1 = sld(&h[1]) * sc, v2 = sld(&h[2]) * sc,
+                  v3 = sld(&h[3]) * sc;
+            float nx = (j4 + 4 < bw) ? sld(src + 4) * sc : 0.0f;
+            float4 *dst = (float4 *)(wt + r * TB_S2 + j4);
+            dst[0] = make_float4(v0, v1, v1, v2);
+            dst[1] = make_float4(v2, v3, v3, nx);
           }
         }
       }
