@@ -339,6 +339,9 @@ def run_ours(args, rank, world, local_rank):
     w = synth.workload(args.workload)
     desc = w.desc_dict()
     geom = api.Geometry(desc, w.matrices(), w.orbit.vdl)
+    # tile and chunk sizes picked by the autotuner (cached per problem shape)
+    from paper_2410_14900_gb300 import tune
+    tuned = tune.autotune(geom, args.storage, chunks=(8, 12, 16, 19, 24), nzs=(16, 32))
     # every rank reconstructs its own seeded phantom (independent problems)
     from paper_2410_14900_gb300 import sharding
     blobs = synth.random_ellipsoids(np.random.default_rng(sharding.rank_seed(w.seed, rank)),
@@ -510,6 +513,7 @@ def run_ours(args, rank, world, local_rank):
                            "planes": [w.n_mu, w.n_s], "volume": list(w.vol_shape),
                            "voxel_mm": list(w.voxel), "storage": args.storage,
                            "batch_per_gpu": B, "parallelism": f"replicas x{world}",
+                           "tuning": {k: tuned[k] for k in ("chunk_images", "bp_nz")},
                            "l2": "inputs larger than L2 (g 390 MB, f 537 MB), no flush"},
                 "roofline": roof, "breakdown": breakdown, "forms": forms, "train_step": train,
                 "batched": batched,

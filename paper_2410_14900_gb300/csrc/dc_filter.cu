@@ -402,7 +402,7 @@ constexpr int BP2_NQ = 2;   // x positions per thread (lane, lane+32)
 constexpr int BP2_RY = 4;   // rows per warp
 constexpr int BP2_TX = 32 * BP2_NQ;
 constexpr int BP2_TY = 8 * BP2_RY;
-constexpr int BP2_MC = 16;  // angles per stage
+constexpr int BP2_MC = 12;  // angles per stage (2 stages: 4 CTAs per SM at 512 s-bins)
 
 enum { OUT_F32 = 0, OUT_BF16 = 1, OUT_F32_ABSMAX = 2 };
 
@@ -821,8 +821,9 @@ int alloc_workspace(dc_geometry *g) {
   g->imgT_stride = (size_t)d.det_cols * g->Hp;
   g->sino_stride = (size_t)d.n_mu * g->NSp;
   size_t per_img = (g->img_stride + g->imgT_stride + 2 * g->sino_stride) * sizeof(float);
-  // keep one chunk's work area near 80 MB so that it stays resident in L2
-  long target = 80L << 20;
+  // size the work area near 112 MB (resident in the 126 MB L2); the
+  // autotuner may use fewer images per chunk than it holds
+  long target = 112L << 20;
   const char *env = getenv("DC_CHUNK_IMAGES");
   int ci = env ? atoi(env) : (int)(target / (long)per_img);
   if (ci < 4) ci = 4;

@@ -111,6 +111,32 @@ def tilted_sinusoid_orbit(n_views: int, sid: float = SID_MM, sdd: float = SDD_MM
     return Orbit("tilted_sinusoid", a, lx, ly, lz, da * dth, sdd, True)
 
 
+def random_nn_orbit(n_views: int = 400, sid: float = SID_MM, sdd: float = SDD_MM,
+                    tilt_deg: float = 10.0, seed: int = 0) -> Orbit:
+    """Random points on the sphere band |tilt| <= tilt_deg (azimuth U[0, 2pi),
+    tilt U[-tilt_deg, tilt_deg]), ordered into a path by nearest neighbour
+    from the first point (Sec. 4.4).  Open orbit; tangents from central
+    differences of the ordered positions (one-sided at the ends)."""
+    rng = np.random.default_rng(seed)
+    th = rng.uniform(0.0, 2.0 * math.pi, n_views)
+    ph = np.radians(rng.uniform(-tilt_deg, tilt_deg, n_views))
+    pts = sid * np.stack([np.cos(ph) * np.cos(th), np.cos(ph) * np.sin(th), np.sin(ph)], 1)
+    order = [0]
+    left = set(range(1, n_views))
+    while left:
+        last = pts[order[-1]]
+        nxt = min(left, key=lambda j: float(np.sum((pts[j] - last) ** 2)))
+        order.append(nxt)
+        left.remove(nxt)
+    a = pts[order]
+    v = np.zeros_like(a)
+    v[1:-1] = 0.5 * (a[2:] - a[:-2])
+    v[0] = a[1] - a[0]
+    v[-1] = a[-1] - a[-2]
+    lx, ly, lz = _frame(a)
+    return Orbit("random_nn", a, lx, ly, lz, v, sdd, False)
+
+
 def circle_arc_orbit(n_circle: int = 360, n_arc: int = 136, sid: float = SID_MM,
                      sdd: float = SDD_MM, arc_deg: float = 60.0) -> Orbit:
     """Full circle plus a perpendicular arc through the circle point phi=0.
