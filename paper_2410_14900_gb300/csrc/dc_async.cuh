@@ -55,7 +55,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
 }
 
 // Wait for phase `parity` of the barrier, giving up after ~2^31 cycles
-// (about one second).  Returns false (and raises bit 1 of *err) on timeout.
+// (about one second).  Returns false (and sets bit 0 of *err) on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity,
                                                   unsigned *err) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -84,6 +84,23 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int x, 
       : "memory");
 }
 
+// 4-byte asynchronous global->shared copy (no alignment beyond the element),
+// grouped by commit and completed by wait_group
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// wait until at most N of this thread's committed groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // single-instruction approximate reciprocal (relative error below 2^-22)
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
@@ -91,15 +108,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// floor of |x| < 2^22 without the conversion pipe: returns the integer and
-// writes the fraction.  At exact integers the result may be n-1 with
-// fraction 1, which every caller here treats identically to (n, 0) because
-// the interpolation weights are continuous.
+// Exact floor of |x| < 2^22 in three FP32 operations, off the conversion
+// pipe: x + 1.5*2^23 rounded toward -inf is floor(x) + 1.5*2^23 (the sum has
+// unit spacing), whose low mantissa bits hold floor(x).  Returns floor(x)
+// and writes the exact fraction x - floor(x) in [0, 1).
 __device__ __forceinline__ int floor_frac(float x, float &frac) {
   const float M = 12582912.0f;  // 1.5 * 2^23
-  float t = (x - 0.5f) + M;
-  float xf = t - M;
-  frac = x - xf;
+  float t = __fadd_rd(x, M);
+  frac = x - (t - M);
   return __float_as_int(t) - 0x4B400000;
 }
 

@@ -131,11 +131,9 @@ struct dc_geometry {
   int chunk_capacity;        // images the work area was sized for
   int bp_nz;                 // voxels per thread along z in the backprojector (16, 32)
   size_t img_stride;         // floats per padded image  (H * Wp)
-  size_t imgT_stride;        // floats per padded transposed image (W * Hp)
   size_t sino_stride;        // floats per padded sinogram (n_mu * NSp)
-  int Wp, Hp, NSp;           // padded row lengths (multiples of 4)
+  int Wp, NSp;               // padded row lengths (multiples of 4)
   float *w_img;              // [chunk][H][Wp]
-  float *w_imgT;             // [chunk][W][Hp]
   float *w_sinoA;            // [chunk][n_mu][NSp]
   float *w_sinoB;            // [chunk][n_mu][NSp]
   unsigned *w_absmax;        // [chunk]

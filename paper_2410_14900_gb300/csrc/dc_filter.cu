@@ -43,27 +43,26 @@ enum { WT_NONE = 0, WT_COS = 1, WT_D = 2 };
 struct PrepArgs {
   const float *src;  // [B][V][H][W]
   float *img;        // [n][H][Wp]
-  float *imgT;       // [n][W][Hp]
   const dc::FView *fv;
-  int H, W, Wp, Hp, V, B, v0, n_img;  // B = batch items in this chunk
-  int b0, Bt;                         // first item of the chunk, total batch
+  int H, W, Wp, V, B, v0, n_img;  // B = batch items in this chunk
+  int b0, Bt;                     // first item of the chunk, total batch
   float pitch;
   int weight;
 };
 
-// 32x32 tiles, transposed through shared memory; pads are written as zeros.
+// weighted copy into rows padded to Wp (the pads are written as zeros)
 __global__ void __launch_bounds__(256) k_prep(PrepArgs a) {
-  __shared__ float tile[32][33];
   int n = blockIdx.z;
   int v = a.v0 + n / a.B, b = a.b0 + n % a.B;
   const dc::FView f = a.fv[v];
   const float *src = a.src + ((size_t)b * a.V + v) * a.H * a.W;
-  int j0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  int tx = threadIdx.x, ty = threadIdx.y;
-  for (int q = ty; q < 32; q += 8) {
-    int r = r0 + q, j = j0 + tx;
+  int j = blockIdx.x * 32 + threadIdx.x;
+  if (j >= a.Wp) return;
+  for (int q = threadIdx.y; q < 32; q += 8) {
+    int r = blockIdx.y * 32 + q;
+    if (r >= a.H) break;
     float val = 0.0f;
-    if (r < a.H && j < a.W) {
+    if (j < a.W) {
       val = src[(size_t)r * a.W + j];
       if (a.weight != WT_NONE) {
         float x = (j - f.cu) * a.pitch, y = (r - f.cv) * a.pitch;
@@ -71,13 +70,7 @@ __global__ void __launch_bounds__(256) k_prep(PrepArgs a) {
         val *= (a.weight == WT_COS) ? f.D * rsqrtf(l2) : l2;
       }
     }
-    tile[q][tx] = val;
-    if (r < a.H && j < a.Wp) a.img[((size_t)n * a.H + r) * a.Wp + j] = val;
-  }
-  __syncthreads();
-  for (int q = ty; q < 32; q += 8) {
-    int j = j0 + q, r = r0 + tx;
-    if (j < a.W && r < a.Hp) a.imgT[((size_t)n * a.W + j) * a.Hp + r] = tile[tx][q];
+    a.img[((size_t)n * a.H + r) * a.Wp + j] = val;
   }
 }
 
@@ -88,11 +81,14 @@ constexpr int LS_THREADS = 256;
 constexpr int LS_WARPS = LS_THREADS / 32;
 constexpr int LS_RB = 16;    // detector rows per band
 constexpr int LS_TPW = 16;   // max (angle, 31-line chunk) tasks per warp
+constexpr int LS_SQ = LS_RB + 1;  // floats per staged sample: odd, so lanes at
+                                  // distinct samples hit distinct banks
+constexpr int LS_PJ = 2;     // zero samples staged on each side of a line
+static_assert(LS_RB == 16, "the column-branch copy maps 16 threads to a band");
 
 struct LineArgs {
   const float *img;   // [n][H][Wp]
-  const float *imgT;  // [n][W][Hp]
-  int H, W, Wp, Hp;
+  int H, W, Wp;
   int n_mu, n_s, NSp;
   int V, B, v0, n_img;  // B = batch items in this chunk
   int b0;               // first batch item of the chunk
@@ -119,14 +115,35 @@ struct LineMu {
   float jscale;      // p / |cs|
 };
 
+// Joseph sum of one line over the nr steps of a staged band: the sample at
+// step q sits at fb + q*dxi samples from the band anchor `base` and is
+// interpolated linearly between its two neighbours.  NR = LS_RB unrolls the
+// band so that the step offset q is an immediate; NR = 0 takes nr at run
+// time.  CLAMP pins positions to [lo, hi], inside the zero pads.
+template <bool CLAMP, int NR>
+__device__ __forceinline__ float band_sum(const float *base, int nr, float fb, float dxi, float lo,
+                                          float hi) {
+  float sum = 0.0f;
+#pragma unroll
+  for (int q = 0; q < (NR ? NR : LS_RB); ++q) {
+    if (!NR && q >= nr) break;
+    float x = fmaf((float)q, dxi, fb);
+    if (CLAMP) x = fminf(fmaxf(x, lo), hi);
+    float f;
+    const float *p = base + dc::floor_frac(x, f) * LS_SQ + q;
+    const float g0 = p[0], g1 = p[LS_SQ];
+    sum += fmaf(f, g1 - g0, g0);
+  }
+  return sum;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(LS_THREADS, 2) k_linesum(LineArgs a) {
   constexpr bool DIFF = (MODE != M_RAW);
   constexpr int STRIDE_L = DIFF ? 31 : 32;  // lines per task (diff: one overlap)
   extern __shared__ __align__(16) float smem[];
-  __shared__ uint64_t bars[2];
   __shared__ LineMu lmu[8];
-  __shared__ int sh_err;
+  __shared__ short2 ttab[LS_TPW * LS_WARPS];
 
   const int n = blockIdx.y;
   const dc::MuGroup G = a.groups[blockIdx.x];
@@ -134,23 +151,18 @@ __global__ void __launch_bounds__(LS_THREADS, 2) k_linesum(LineArgs a) {
   const dc::FView fv = a.fv[v];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // streamed image: branch 0 steps over detector rows of img, branch 1 over
-  // detector columns, i.e. the rows of the transposed image
-  const int rows = G.branch ? a.W : a.H;   // steps along a line
-  const int len = G.branch ? a.H : a.W;    // samples across a line
-  const int lenp = G.branch ? a.Hp : a.Wp;
-  const int rstride = lenp + PADL + PADR;
-  const float *src = G.branch ? a.imgT + (size_t)n * a.W * a.Hp : a.img + (size_t)n * a.H * a.Wp;
+  // branch 0 steps over detector rows and samples along a row; branch 1
+  // steps over detector columns and samples along a column.  Either way a
+  // band of LS_RB steps is staged as [sample][LS_SQ]: the band position q is
+  // the fastest index, so inside the unrolled band loop it is an immediate.
+  const int rows = G.branch ? a.W : a.H;  // steps along a line
+  const int len = G.branch ? a.H : a.W;   // samples across a line
+  const float *src = a.img + (size_t)n * a.H * a.Wp;
+  const int stage_sz = (len + 2 * LS_PJ) * LS_SQ;
   float *stage0 = smem;
-  float *stage1 = smem + LS_RB * rstride;
-  float *ep = smem + 2 * LS_RB * rstride;  // [mg][NSp] epilogue buffer
+  float *stage1 = smem + stage_sz;
+  float *ep = smem + 2 * stage_sz;  // [mg][NSp] epilogue buffer
 
-  if (threadIdx.x == 0) {
-    dc::mbar_init(&bars[0], 1);
-    dc::mbar_init(&bars[1], 1);
-    dc::fence_barrier_init();
-    sh_err = 0;
-  }
   if (threadIdx.x < G.count) {
     int m = a.mu_order[G.first + threadIdx.x];
     const dc::MuRec R = a.mu[m];
@@ -166,80 +178,72 @@ __global__ void __launch_bounds__(LS_THREADS, 2) k_linesum(LineArgs a) {
     L.jscale = R.jscale;
     lmu[threadIdx.x] = L;
   }
-  // zero the row pads of both stages (never written by the bulk copies)
-  for (int i = threadIdx.x; i < 2 * LS_RB; i += LS_THREADS) {
-    float *row = smem + (size_t)i * rstride;
-    for (int t = 0; t < PADL; ++t) row[t] = 0.0f;
-    for (int t = PADL + lenp; t < rstride; ++t) row[t] = 0.0f;
+  // zero the sample pads of both stages (never written by the copies)
+  for (int i = threadIdx.x; i < 2 * 2 * LS_PJ * LS_SQ; i += LS_THREADS) {
+    int st = i / (2 * LS_PJ * LS_SQ), r = i % (2 * LS_PJ * LS_SQ);
+    int jj = r / LS_SQ, q = r % LS_SQ;
+    int row = jj < LS_PJ ? jj : len + jj;  // samples -PJ..-1 and len..len+PJ-1
+    smem[(size_t)st * stage_sz + (size_t)row * LS_SQ + q] = 0.0f;
   }
   __syncthreads();
 
+  // asynchronous 4-byte copies into the interleaved layout (coalesced reads)
   const int nbands = (rows + LS_RB - 1) / LS_RB;
-  auto issue = [&](int band) {
-    int r0 = band * LS_RB;
-    int nr = min(LS_RB, rows - r0);
-    uint64_t *bar = &bars[band & 1];
-    float *st = (band & 1) ? stage1 : stage0;
-    dc::fence_proxy_async();
-    dc::mbar_arrive_expect_tx(bar, (unsigned)(nr * lenp * 4));
-    for (int q = 0; q < nr; ++q)
-      dc::bulk_g2s(st + (size_t)q * rstride + PADL, src + (size_t)(r0 + q) * lenp,
-                   (unsigned)(lenp * 4), bar);
-  };
-  if (threadIdx.x == 0) {
-    issue(0);
-    if (nbands > 1) issue(1);
-  }
-
-  // tasks: (angle of the group, chunk of STRIDE_L lines); lane = line in chunk
-  const int nch = (a.n_s - (DIFF ? 1 : 0) + STRIDE_L - 1) / STRIDE_L;
-  const int ntask = G.count * nch;
-  int X0i[LS_TPW];
-  float x0f[LS_TPW], acc[LS_TPW];
-#pragma unroll
-  for (int tt = 0; tt < LS_TPW; ++tt) {
-    acc[tt] = 0.0f;
-    X0i[tt] = 0;
-    x0f[tt] = 0.0f;
-    int t = warp + LS_WARPS * tt;
-    if (t < ntask) {
-      const LineMu &L = lmu[t / nch];
-      int k = (t % nch) * STRIDE_L + lane;
-      k = min(k, a.n_s - 1);
-      float kk = (float)k - 0.5f * (float)(a.n_s - 1);  // half-integer or integer
-      // x0 = b0 + kk * A, split into integer and fraction without FP64
-      float t1 = kk * L.a_hi;  // exact
-      float t1i = floorf(t1);
-      float fr = L.b0f + (t1 - t1i) + kk * L.a_lo;
-      float fri = floorf(fr);
-      X0i[tt] = (int)L.b0i + (int)t1i + (int)fri;
-      x0f[tt] = fr - fri;
-    }
-  }
-
-  bool ok = true;
-  for (int band = 0; band < nbands; ++band) {
-    if (!dc::mbar_wait_bounded(&bars[band & 1], (band >> 1) & 1, a.err)) ok = false;
-    if (__syncthreads_or(!ok)) {
-      ok = false;
-      break;
-    }
-    const float *st = (band & 1) ? stage1 : stage0;
+  auto stage = [&](int band) {
+    float *st = ((band & 1) ? stage1 : stage0) + LS_PJ * LS_SQ;
     const int r0 = band * LS_RB;
     const int nr = min(LS_RB, rows - r0);
-#pragma unroll
-    for (int tt = 0; tt < LS_TPW; ++tt) {
-      int t = warp + LS_WARPS * tt;
-      if (t >= ntask) break;
-      const LineMu &L = lmu[t / nch];
-      // anchor of this band: xi(r0) = J + fb, exactly split
-      float r0f = (float)r0;
-      float th = r0f * L.d_hi;  // exact
-      float thi = floorf(th);
-      float fr = x0f[tt] + (th - thi) + r0f * L.d_lo;
-      float fri = floorf(fr);
-      int J = X0i[tt] + (int)thi + (int)fri;
-      float fb = fr - fri;
+    if (!G.branch) {
+      for (int q = 0; q < nr; ++q) {
+        const float *s = src + (size_t)(r0 + q) * a.Wp;
+        for (int jj = threadIdx.x; jj < len; jj += LS_THREADS) dc::cp_async4(st + jj * LS_SQ + q, s + jj);
+      }
+    } else {
+      const int q = threadIdx.x % LS_RB;
+      if (q < nr)
+        for (int jj = threadIdx.x / LS_RB; jj < len; jj += LS_THREADS / LS_RB)
+          dc::cp_async4(st + jj * LS_SQ + q, src + (size_t)jj * a.Wp + r0 + q);
+    }
+    dc::cp_async_commit();
+  };
+  stage(0);
+
+  // tasks: (angle of the group, chunk of STRIDE_L lines); lane = line in
+  // chunk.  Each line accumulates straight into its epilogue slot ep[ml][k]
+  // (a lane owns one slot per task), so the task loop needs no registers per
+  // task and stays rolled.
+  const int nch = (a.n_s - (DIFF ? 1 : 0) + STRIDE_L - 1) / STRIDE_L;
+  const int ntask = G.count * nch;
+  for (int t = threadIdx.x; t < ntask; t += LS_THREADS)
+    ttab[t] = make_short2((short)(t / nch), (short)((t % nch) * STRIDE_L));
+  for (int i = threadIdx.x; i < G.count * a.NSp; i += LS_THREADS) ep[i] = 0.0f;
+  const float kc = 0.5f * (float)(a.n_s - 1);
+
+  for (int band = 0; band < nbands; ++band) {
+    if (band + 1 < nbands) {
+      stage(band + 1);
+      dc::cp_async_wait<1>();
+    } else {
+      dc::cp_async_wait<0>();
+    }
+    __syncthreads();
+    const float *st = ((band & 1) ? stage1 : stage0) + LS_PJ * LS_SQ;
+    const int r0 = band * LS_RB;
+    const int nr = min(LS_RB, rows - r0);
+    const float r0f = (float)r0;
+    for (int t = warp; t < ntask; t += LS_WARPS) {
+      const short2 tk = ttab[t];
+      const LineMu &L = lmu[tk.x];
+      const int k = min(tk.y + lane, a.n_s - 1);
+      // anchor xi(r0) = b0 + kk*A + r0*d = J + fb, exactly split: kk*a_hi and
+      // r0*d_hi are exact products, the low parts add below 2^-12
+      const float kk = (float)k - kc;  // half-integer or integer
+      const float t1 = kk * L.a_hi, th = r0f * L.d_hi;
+      const float t1i = floorf(t1), thi = floorf(th);
+      const float fr = L.b0f + (t1 - t1i) + (th - thi) + fmaf(kk, L.a_lo, r0f * L.d_lo);
+      const float fri = floorf(fr);
+      const int J = (int)L.b0i + (int)t1i + (int)thi + (int)fri;
+      const float fb = fr - fri;
       const float dxi = L.dxi;
       float lo = (float)(-1 - J), hi = (float)(len - J);
       float xa = fb, xb = fmaf((float)(nr - 1), dxi, fb);
@@ -247,55 +251,26 @@ __global__ void __launch_bounds__(LS_THREADS, 2) k_linesum(LineArgs a) {
       bool outside = (xmax <= lo) || (xmin >= hi);
       if (__all_sync(0xffffffffu, outside)) continue;  // the band misses these lines
       bool inside = (xmin >= lo + 1.0f) && (xmax <= hi - 1.0f);
-      const float *base = st + PADL + J;
-      float sum = 0.0f;
-      if (__all_sync(0xffffffffu, inside)) {
-        float qf = 0.0f;
-#pragma unroll 4
-        for (int q = 0; q < nr; ++q, qf += 1.0f) {
-          float f;
-          int j = dc::floor_frac(fmaf(qf, dxi, fb), f);
-          const float *p = base + q * rstride + j;
-          float g0 = p[0], g1 = p[1];
-          sum += fmaf(f, g1 - g0, g0);
-        }
-      } else {
-        float qf = 0.0f;
-#pragma unroll 4
-        for (int q = 0; q < nr; ++q, qf += 1.0f) {
-          float f;
-          int j = dc::floor_frac(fminf(fmaxf(fmaf(qf, dxi, fb), lo), hi), f);
-          const float *p = base + q * rstride + j;
-          float g0 = p[0], g1 = p[1];
-          sum += fmaf(f, g1 - g0, g0);
-        }
-      }
+      const float *base = st + J * LS_SQ;
+      float sum;
+      if (nr == LS_RB)
+        sum = __all_sync(0xffffffffu, inside) ? band_sum<false, LS_RB>(base, LS_RB, fb, dxi, lo, hi)
+                                              : band_sum<true, LS_RB>(base, LS_RB, fb, dxi, lo, hi);
+      else
+        sum = band_sum<true, 0>(base, nr, fb, dxi, lo, hi);
+      const int kl = tk.y + lane;
       if (DIFF) {
         float nb = __shfl_down_sync(0xffffffffu, sum, 1);
-        acc[tt] += nb - sum;
+        if (lane < 31 && kl <= a.n_s - 2) ep[tk.x * a.NSp + kl] += nb - sum;
       } else {
-        acc[tt] += sum;
+        if (kl <= a.n_s - 1) ep[tk.x * a.NSp + kl] += sum;
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && band + 2 < nbands) issue(band + 2);
-  }
-  if (!ok) {
-    // drain: give the copies still in flight a bounded chance to land
-    for (int s = 0; s < 2; ++s) dc::mbar_wait_bounded(&bars[s], 0, nullptr);
-    return;
   }
 
-  // line sums (RAW) or differences R_{k+1}-R_k (DIFF) into the epilogue buffer
-#pragma unroll
-  for (int tt = 0; tt < LS_TPW; ++tt) {
-    int t = warp + LS_WARPS * tt;
-    if (t >= ntask) break;
-    int ml = t / nch;
-    int k = (t % nch) * STRIDE_L + lane;
-    bool valid = DIFF ? (lane < 31 && k <= a.n_s - 2) : (k <= a.n_s - 1);
-    if (valid) ep[ml * a.NSp + k] = acc[tt] * lmu[ml].jscale;
-  }
+  // line sums (RAW) or differences R_{k+1}-R_k (DIFF), times the Joseph scale
+  for (int i = threadIdx.x; i < G.count * a.NSp; i += LS_THREADS) ep[i] *= lmu[i / a.NSp].jscale;
   __syncthreads();
 
   const float D = fv.D, D2 = D * D;
@@ -661,9 +636,12 @@ __global__ void k_sino_in(const float *__restrict__ R, const dc::MuRec *__restri
 
 int round4(int x) { return (x + 3) & ~3; }
 
+size_t linesum_smem_for(int H, int W, int mg, int NSp) {
+  return (size_t)(2 * (std::max(H, W) + 2 * LS_PJ) * LS_SQ + mg * NSp) * sizeof(float);
+}
+
 size_t linesum_smem(const dc_geometry *g) {
-  int lenp = std::max(g->Wp, g->Hp);
-  return (size_t)(2 * LS_RB * (lenp + PADL + PADR) + g->mg * g->NSp) * sizeof(float);
+  return linesum_smem_for(g->d.det_rows, g->d.det_cols, g->mg, g->NSp);
 }
 
 size_t bp2d_smem(const dc_geometry *g) {
@@ -707,12 +685,10 @@ int launch_prep(const dc_geometry *g, const float *src, int weight, int v0, int 
   PrepArgs p;
   p.src = src;
   p.img = g->w_img;
-  p.imgT = g->w_imgT;
   p.fv = g->fv;
   p.H = d.det_rows;
   p.W = d.det_cols;
   p.Wp = g->Wp;
-  p.Hp = g->Hp;
   p.V = d.n_views;
   p.B = B;
   p.v0 = v0;
@@ -721,8 +697,7 @@ int launch_prep(const dc_geometry *g, const float *src, int weight, int v0, int 
   p.n_img = n_img;
   p.pitch = (float)d.pitch;
   p.weight = weight;
-  dim3 grid((std::max(g->Wp, d.det_cols) + 31) / 32, (std::max(g->Hp, d.det_rows) + 31) / 32,
-            n_img);
+  dim3 grid((g->Wp + 31) / 32, (d.det_rows + 31) / 32, n_img);
   dc::ProfScope ps(dc::KID_PREP, st);
   k_prep<<<grid, dim3(32, 8), 0, st>>>(p);
   DC_CHECK_LAUNCH("k_prep");
@@ -734,11 +709,9 @@ LineArgs line_args(const dc_geometry *g, int B, int v0, int b0, int n_img) {
   LineArgs a;
   memset(&a, 0, sizeof(a));
   a.img = g->w_img;
-  a.imgT = g->w_imgT;
   a.H = d.det_rows;
   a.W = d.det_cols;
   a.Wp = g->Wp;
-  a.Hp = g->Hp;
   a.n_mu = d.n_mu;
   a.n_s = d.n_s;
   a.NSp = g->NSp;
@@ -815,12 +788,10 @@ namespace dc {
 int alloc_workspace(dc_geometry *g) {
   const dc_geometry_desc &d = g->d;
   g->Wp = round4(d.det_cols);
-  g->Hp = round4(d.det_rows);
   g->NSp = round4(d.n_s);
   g->img_stride = (size_t)d.det_rows * g->Wp;
-  g->imgT_stride = (size_t)d.det_cols * g->Hp;
   g->sino_stride = (size_t)d.n_mu * g->NSp;
-  size_t per_img = (g->img_stride + g->imgT_stride + 2 * g->sino_stride) * sizeof(float);
+  size_t per_img = (g->img_stride + 2 * g->sino_stride) * sizeof(float);
   // size the work area near 112 MB (resident in the 126 MB L2); the
   // autotuner may use fewer images per chunk than it holds
   long target = 112L << 20;
@@ -834,7 +805,6 @@ int alloc_workspace(dc_geometry *g) {
   if (linesum_smem(g) > 200 * 1024 || bp2d_smem(g) > 200 * 1024)
     return fail(DC_ERR_UNSUPPORTED, "detector or sinogram rows too long for shared memory");
   DC_CUDA(dmalloc((void **)&g->w_img, sizeof(float) * g->img_stride * ci));
-  DC_CUDA(dmalloc((void **)&g->w_imgT, sizeof(float) * g->imgT_stride * ci));
   DC_CUDA(dmalloc((void **)&g->w_sinoA, sizeof(float) * g->sino_stride * ci));
   DC_CUDA(dmalloc((void **)&g->w_sinoB, sizeof(float) * g->sino_stride * ci));
   DC_CUDA(dmalloc((void **)&g->w_absmax, sizeof(unsigned) * ci));
@@ -1106,8 +1076,8 @@ extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, do
   if (n_mu > NA_MAX_MU)
     return dc::fail(DC_ERR_ARG, "dc_radon2d_noalloc: n_mu above the fixed maximum of " +
                                     std::to_string(NA_MAX_MU));
-  const int Wp = round4(W), Hp = round4(H), NSp = round4(n_s);
-  const size_t per_img = ((size_t)H * Wp + (size_t)W * Hp) * sizeof(float);
+  const int Wp = round4(W), NSp = round4(n_s);
+  const size_t per_img = (size_t)H * Wp * sizeof(float);
   const size_t cap = NA_BYTES - NA_TABLE_BYTES;
   if (per_img > cap)
     return dc::fail(DC_ERR_ARG, "dc_radon2d_noalloc: one " + std::to_string(H) + "x" +
@@ -1116,8 +1086,7 @@ extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, do
                                     "maximum is " + std::to_string(cap) + " bytes");
   int chunks = (n_s - 1 + 30) / 31;
   int mg = std::max(1, std::min(8, (16 * 8) / std::max(1, chunks)));
-  size_t smem = (size_t)(2 * LS_RB * (std::max(Wp, Hp) + PADL + PADR) + mg * NSp) *
-                sizeof(float);
+  size_t smem = linesum_smem_for(H, W, mg, NSp);
   if (smem > 200 * 1024)
     return dc::fail(DC_ERR_UNSUPPORTED, "dc_radon2d_noalloc: rows too long for shared memory");
 
@@ -1163,16 +1132,13 @@ extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, do
   float *img_w = work;
   for (int n0 = 0; n0 < n_img; n0 += per_chunk) {
     int nc = std::min(per_chunk, n_img - n0);
-    float *imgT_w = img_w + (size_t)nc * H * Wp;
     PrepArgs p;
     p.src = img + (size_t)n0 * H * W;
     p.img = img_w;
-    p.imgT = imgT_w;
     p.fv = fv;
     p.H = H;
     p.W = W;
     p.Wp = Wp;
-    p.Hp = Hp;
     p.V = 1;    // image n is batch item n of a one-view problem, so it
     p.B = nc;   // reads offset n*H*W and table record 0
     p.v0 = 0;
@@ -1181,7 +1147,7 @@ extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, do
     p.n_img = nc;
     p.pitch = (float)pitch;
     p.weight = WT_NONE;
-    dim3 gp((std::max(Wp, W) + 31) / 32, (std::max(Hp, H) + 31) / 32, nc);
+    dim3 gp((Wp + 31) / 32, (H + 31) / 32, nc);
     {
       dc::ProfScope ps(dc::KID_PREP, st);
       k_prep<<<gp, dim3(32, 8), 0, st>>>(p);
@@ -1190,11 +1156,9 @@ extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, do
     LineArgs a;
     memset(&a, 0, sizeof(a));
     a.img = img_w;
-    a.imgT = imgT_w;
     a.H = H;
     a.W = W;
     a.Wp = Wp;
-    a.Hp = Hp;
     a.n_mu = n_mu;
     a.n_s = n_s;
     a.NSp = NSp;

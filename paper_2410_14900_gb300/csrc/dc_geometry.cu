@@ -161,7 +161,6 @@ void free_geometry(dc_geometry *g) {
   cudaFree(g->mu_order);
   cudaFree(g->groups);
   cudaFree(g->w_img);
-  cudaFree(g->w_imgT);
   cudaFree(g->w_sinoA);
   cudaFree(g->w_sinoB);
   cudaFree(g->w_absmax);

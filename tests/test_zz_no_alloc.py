@@ -56,7 +56,7 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
     Lh = L.load()
     x = torch.zeros(4, device="cuda")
     ptr = ctypes.c_void_p(x.data_ptr())
-    # one 4096 x 4096 image needs 128 MiB of work area: more than the fixed 32 MiB
+    # one 4096 x 4096 image needs 64 MiB of work area: more than the fixed 32 MiB
     rc = Lh.dc_radon2d_noalloc(1, 4096, 4096, 90, 4096, 1.0, 1.0, 2047.5, 2047.5, ptr, ptr, None)
     assert rc == L.DC_ERR_ARG
     assert b"fixed" in Lh.dc_last_error()
