@@ -251,13 +251,23 @@ template <>
 __device__ __forceinline__ float sld<__half>(const __half *p) { return __half2float(*p); }
 
 // Shared memory of k_bp3d_tma (dynamic): NS raw TMA stages, then two FP32
-// work tiles of interleaved tap pairs (g[r][j], g[r][j+1]) with a row stride
+// work tiles of tap pairs (g[r][j], g[r][j+1] - g[r][j]) with a row stride
 // of TB_S2 float2 (8 mod 16): adjacent rows put one column on different
-// banks, and a bilinear row pair is one 64-bit load.
+// banks, a row's linear interpolation is one 64-bit load and one FMA.
 constexpr int TB_S2 = TB_BWW + 8;
 template <typename T>
 constexpr size_t bp_tma_smem() {
   return (size_t)TB_NS * TB_BH * TB_BWW * sizeof(T) + 2 * (size_t)TB_BH * TB_S2 * sizeof(float2);
+}
+
+// Tap addressing without integer conversions: x + kM rounded toward -inf is
+// floor(x) + kM (unit spacing below 2^24), whose bit pattern is
+// kFloorBits + floor(x); tile byte offsets fold kFloorBits in once per view.
+constexpr float kM = 12582912.0f;  // 1.5 * 2^23
+constexpr unsigned kFloorBits = 0x4B400000u;
+
+__device__ __forceinline__ float2 ldpair(const char *sb, unsigned off) {
+  return *reinterpret_cast<const float2 *>(sb + off);
 }
 
 // One CTA backprojects one box of 16 x 16 x NZ voxels (box indices bxi, byi
@@ -271,6 +281,7 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
                                        dc::BPView *sv, int4 *vtab, unsigned &it) {
   constexpr size_t STAGE_BYTES = (size_t)TB_BH * TB_BWW * sizeof(T);
   float2 *wtile0 = (float2 *)(dsm + TB_NS * STAGE_BYTES);
+  const char *sb = reinterpret_cast<const char *>(dsm);
 
   const int tid = threadIdx.y * TB_TX + threadIdx.x;
   const int ix = bxi * TB_TX + threadIdx.x;
@@ -371,6 +382,9 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
       if (a.scale) sc = a.scale[(size_t)b * a.V + i];
       bool w_ok = dc::mbar_wait_bounded(&full[s], (it / TB_NS) & 1, err);
       float2 *wt = wtile0 + (size_t)(it & 1) * TB_BH * TB_S2;
+      const unsigned wt_off = (unsigned)((const unsigned char *)wt - dsm);  // bytes
+      // tile byte offset minus the floor's exponent bits of a row and a column
+      const unsigned cbg = wt_off - kFloorBits * (unsigned)(TB_S2 * 8 + 8);
       const bool staged = (t.z == FP_NARROW || t.z == FP_WIDE);
       if (w_ok && staged) {
         // raw box -> FP32 pair tile (times the FP16 scale)
@@ -386,8 +400,8 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
             float4 v = *(const float4 *)src;
             float nx = (j4 + 4 < bw) ? src[4] : 0.0f;
             float4 *dst = (float4 *)(wt + r * TB_S2 + j4);
-            dst[0] = make_float4(v.x, v.y, v.y, v.z);
-            dst[1] = make_float4(v.z, v.w, v.w, nx);
+            dst[0] = make_float4(v.x, v.y - v.x, v.y, v.z - v.y);
+            dst[1] = make_float4(v.z, v.w - v.z, v.w, nx - v.w);
           }
         } else {
           // 16-bit storage: four values per 8-byte load, converted (and
@@ -403,8 +417,8 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
                   v3 = sld(&h[3]) * sc;
             float nx = (j4 + 4 < bw) ? sld(src + 4) * sc : 0.0f;
             float4 *dst = (float4 *)(wt + r * TB_S2 + j4);
-            dst[0] = make_float4(v0, v1, v1, v2);
-            dst[1] = make_float4(v2, v3, v3, nx);
+            dst[0] = make_float4(v0, v1 - v0, v1, v2 - v1);
+            dst[1] = make_float4(v2, v3 - v2, v3, nx - v3);
           }
         }
       }
@@ -428,18 +442,20 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
           float rw = dc::rcp_approx(W0);
           float u = fminf(fmaxf(fmaf(U0, rw, cul), 0.0f), umx), fu;
           int j = dc::floor_frac(u, fu);
-          const float2 *col = wt + j;
+          // byte offset of column j, minus the floor's exponent bits per row
+          const unsigned cbc = wt_off + (unsigned)j * 8u - kFloorBits * (unsigned)(TB_S2 * 8);
           float vb = fmaf(V0, rw, cvl), dv = dV * rw;
           // v is affine in k: the column stays inside the tile if both ends do
           float vlast = fmaf((float)(NZ - 1), dv, vb);
           if (fminf(vb, vlast) >= 0.01f && fmaxf(vb, vlast) <= vmx - 0.01f) {
 #pragma unroll
             for (int k = 0; k < NZ; ++k) {
-              float kf = (float)k, fv;
-              int r = dc::floor_frac(fmaf(kf, dv, vb), fv);
-              const float2 *p = col + r * TB_S2;
-              float2 q0 = p[0], q1 = p[TB_S2];
-              float x0 = fmaf(fu, q0.y - q0.x, q0.x), x1 = fmaf(fu, q1.y - q1.x, q1.x);
+              float kf = (float)k;
+              const float v = fmaf(kf, dv, vb);
+              const float tv = __fadd_rd(v, kM), fv = v - (tv - kM);
+              const unsigned off = __float_as_uint(tv) * (unsigned)(TB_S2 * 8) + cbc;
+              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + TB_S2 * 8);
+              float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
               float val = fmaf(fv, x1 - x0, x0);
               float ez = fmaf(kf, a.dz, ez0);
               float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
@@ -456,11 +472,11 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
 #pragma unroll
             for (int k = 0; k < NZ; ++k) {
               float kf = (float)k;
-              float v = fminf(fmaxf(fmaf(kf, dv, vb), 0.0f), vmx), fv;
-              int r = dc::floor_frac(v, fv);
-              const float2 *p = col + r * TB_S2;
-              float2 q0 = p[0], q1 = p[TB_S2];
-              float x0 = fmaf(fu, q0.y - q0.x, q0.x), x1 = fmaf(fu, q1.y - q1.x, q1.x);
+              const float v = fminf(fmaxf(fmaf(kf, dv, vb), 0.0f), vmx);
+              const float tv = __fadd_rd(v, kM), fv = v - (tv - kM);
+              const unsigned off = __float_as_uint(tv) * (unsigned)(TB_S2 * 8) + cbc;
+              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + TB_S2 * 8);
+              float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
               float val = fmaf(fv, x1 - x0, x0);
               float ez = fmaf(kf, a.dz, ez0);
               float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
@@ -488,12 +504,14 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
             for (int k = 0; k < NZ; ++k) {
               float kf = (float)k;
               float rw = dc::rcp_approx(fmaf(kf, dW, W0));
-              float fu, fv;
-              int j = dc::floor_frac(fmaf(fmaf(kf, dU, U0), rw, cul), fu);
-              int r = dc::floor_frac(fmaf(fmaf(kf, dV, V0), rw, cvl), fv);
-              const float2 *p = wt + r * TB_S2 + j;
-              float2 q0 = p[0], q1 = p[TB_S2];
-              float x0 = fmaf(fu, q0.y - q0.x, q0.x), x1 = fmaf(fu, q1.y - q1.x, q1.x);
+              const float u = fmaf(fmaf(kf, dU, U0), rw, cul);
+              const float v = fmaf(fmaf(kf, dV, V0), rw, cvl);
+              const float tu = __fadd_rd(u, kM), tv = __fadd_rd(v, kM);
+              const float fu = u - (tu - kM), fv = v - (tv - kM);
+              const unsigned off = __float_as_uint(tv) * (unsigned)(TB_S2 * 8) +
+                                   __float_as_uint(tu) * 8u + cbg;
+              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + TB_S2 * 8);
+              float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
               float val = fmaf(fv, x1 - x0, x0);
               float ez = fmaf(kf, a.dz, ez0);
               float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
@@ -511,13 +529,14 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
             for (int k = 0; k < NZ; ++k) {
               float kf = (float)k;
               float rw = dc::rcp_approx(fmaf(kf, dW, W0));
-              float u = fminf(fmaxf(fmaf(fmaf(kf, dU, U0), rw, cul), 0.0f), umx);
-              float v = fminf(fmaxf(fmaf(fmaf(kf, dV, V0), rw, cvl), 0.0f), vmx);
-              float fu, fv;
-              int j = dc::floor_frac(u, fu), r = dc::floor_frac(v, fv);
-              const float2 *p = wt + r * TB_S2 + j;
-              float2 q0 = p[0], q1 = p[TB_S2];
-              float x0 = fmaf(fu, q0.y - q0.x, q0.x), x1 = fmaf(fu, q1.y - q1.x, q1.x);
+              const float u = fminf(fmaxf(fmaf(fmaf(kf, dU, U0), rw, cul), 0.0f), umx);
+              const float v = fminf(fmaxf(fmaf(fmaf(kf, dV, V0), rw, cvl), 0.0f), vmx);
+              const float tu = __fadd_rd(u, kM), tv = __fadd_rd(v, kM);
+              const float fu = u - (tu - kM), fv = v - (tv - kM);
+              const unsigned off = __float_as_uint(tv) * (unsigned)(TB_S2 * 8) +
+                                   __float_as_uint(tu) * 8u + cbg;
+              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + TB_S2 * 8);
+              float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
               float val = fmaf(fv, x1 - x0, x0);
               float ez = fmaf(kf, a.dz, ez0);
               float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));

@@ -116,22 +116,27 @@ struct LineMu {
 };
 
 // Joseph sum of one line over the nr steps of a staged band: the sample at
-// step q sits at fb + q*dxi samples from the band anchor `base` and is
-// interpolated linearly between its two neighbours.  NR = LS_RB unrolls the
-// band so that the step offset q is an immediate; NR = 0 takes nr at run
-// time.  CLAMP pins positions to [lo, hi], inside the zero pads.
+// step q sits at fb + q*dxi samples from the band anchor and is interpolated
+// linearly between its two neighbours.  The anchor's byte offset in shared
+// memory is folded with the floor's exponent bits into cb, so one integer
+// multiply-add turns the rounded-down position into the address; NR = LS_RB
+// unrolls the band so that the step offset 4q is an immediate (NR = 0 takes
+// nr at run time).  CLAMP pins positions to [lo, hi], inside the zero pads.
 template <bool CLAMP, int NR>
-__device__ __forceinline__ float band_sum(const float *base, int nr, float fb, float dxi, float lo,
-                                          float hi) {
+__device__ __forceinline__ float band_sum(const char *sb, unsigned cb, int nr, float fb, float dxi,
+                                          float lo, float hi) {
+  const float M = 12582912.0f;  // 1.5 * 2^23: x + M rounded down holds floor(x)
   float sum = 0.0f;
 #pragma unroll
   for (int q = 0; q < (NR ? NR : LS_RB); ++q) {
     if (!NR && q >= nr) break;
     float x = fmaf((float)q, dxi, fb);
     if (CLAMP) x = fminf(fmaxf(x, lo), hi);
-    float f;
-    const float *p = base + dc::floor_frac(x, f) * LS_SQ + q;
-    const float g0 = p[0], g1 = p[LS_SQ];
+    const float t = __fadd_rd(x, M);
+    const float f = x - (t - M);
+    const unsigned off = __float_as_uint(t) * (unsigned)(LS_SQ * 4) + cb + 4u * q;
+    const float g0 = *reinterpret_cast<const float *>(sb + off);
+    const float g1 = *reinterpret_cast<const float *>(sb + off + LS_SQ * 4);
     sum += fmaf(f, g1 - g0, g0);
   }
   return sum;
@@ -162,6 +167,7 @@ __global__ void __launch_bounds__(LS_THREADS, 2) k_linesum(LineArgs a) {
   float *stage0 = smem;
   float *stage1 = smem + stage_sz;
   float *ep = smem + 2 * stage_sz;  // [mg][NSp] epilogue buffer
+  const char *sb = reinterpret_cast<const char *>(smem);
 
   if (threadIdx.x < G.count) {
     int m = a.mu_order[G.first + threadIdx.x];
@@ -227,7 +233,8 @@ __global__ void __launch_bounds__(LS_THREADS, 2) k_linesum(LineArgs a) {
       dc::cp_async_wait<0>();
     }
     __syncthreads();
-    const float *st = ((band & 1) ? stage1 : stage0) + LS_PJ * LS_SQ;
+    // byte offset of sample 0 of this band's stage
+    const int st_off = ((band & 1) ? stage_sz : 0) * 4 + LS_PJ * LS_SQ * 4;
     const int r0 = band * LS_RB;
     const int nr = min(LS_RB, rows - r0);
     const float r0f = (float)r0;
@@ -251,13 +258,14 @@ __global__ void __launch_bounds__(LS_THREADS, 2) k_linesum(LineArgs a) {
       bool outside = (xmax <= lo) || (xmin >= hi);
       if (__all_sync(0xffffffffu, outside)) continue;  // the band misses these lines
       bool inside = (xmin >= lo + 1.0f) && (xmax <= hi - 1.0f);
-      const float *base = st + J * LS_SQ;
+      // byte offset of sample J of this stage, minus the floor's exponent bits
+      const unsigned cb = (unsigned)(st_off + J * LS_SQ * 4) - 0x4B400000u * (unsigned)(LS_SQ * 4);
       float sum;
       if (nr == LS_RB)
-        sum = __all_sync(0xffffffffu, inside) ? band_sum<false, LS_RB>(base, LS_RB, fb, dxi, lo, hi)
-                                              : band_sum<true, LS_RB>(base, LS_RB, fb, dxi, lo, hi);
+        sum = __all_sync(0xffffffffu, inside) ? band_sum<false, LS_RB>(sb, cb, LS_RB, fb, dxi, lo, hi)
+                                              : band_sum<true, LS_RB>(sb, cb, LS_RB, fb, dxi, lo, hi);
       else
-        sum = band_sum<true, 0>(base, nr, fb, dxi, lo, hi);
+        sum = band_sum<true, 0>(sb, cb, nr, fb, dxi, lo, hi);
       const int kl = tk.y + lane;
       if (DIFF) {
         float nb = __shfl_down_sync(0xffffffffu, sum, 1);
@@ -403,6 +411,17 @@ struct BPMu {
   int i00;  // I00 as an integer
 };
 
+// the two sinogram taps around s-bin position x (relative to a row anchor
+// folded into cb, as in band_sum) and the fraction of x past the first
+__device__ __forceinline__ float taps(const char *sb, unsigned cb, float x, float &p0, float &p1) {
+  const float M = 12582912.0f;
+  const float t = __fadd_rd(x, M);
+  const unsigned off = __float_as_uint(t) * 4u + cb;
+  p0 = *reinterpret_cast<const float *>(sb + off);
+  p1 = *reinterpret_cast<const float *>(sb + off + 4);
+  return x - (t - M);
+}
+
 __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
   extern __shared__ __align__(16) float smem[];
   __shared__ uint64_t bars[2];
@@ -416,6 +435,7 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
   const int stage_sz = BP2_MC * rstride;
   const float *src = a.sino + (size_t)n * a.n_mu * a.NSp;
   const int nchunk = (a.n_mu + BP2_MC - 1) / BP2_MC;
+  const char *sb = reinterpret_cast<const char *>(smem);
 
   if (threadIdx.x == 0) {
     dc::mbar_init(&bars[0], 1);
@@ -496,11 +516,12 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
       ok = false;
       break;
     }
-    const float *st = smem + (c & 1) * stage_sz;
+    const int st_off = (c & 1) * stage_sz;  // floats
     int nm = min(BP2_MC, a.n_mu - c * BP2_MC);
     for (int mi = 0; mi < nm; ++mi) {
       const BPMu M = bmu[c & 1][mi];
-      const float *row = st + mi * rstride + PADL + M.i00;
+      // byte offset of s-bin I00 of this angle's row, minus the floor's exponent bits
+      const unsigned cb = (unsigned)((st_off + mi * rstride + PADL + M.i00) * 4) - 4u * 0x4B400000u;
       float w1c = 1.0f - M.winv;
       if (M.pad0 != 0.0f) {
 #pragma unroll
@@ -508,12 +529,11 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
           float rt = fmaf(rlf[ry], M.Bs, M.F00);
 #pragma unroll
           for (int q = 0; q < BP2_NQ; ++q) {
-            float f;
-            int k = dc::floor_frac(fmaf(jlf[q], M.Bc, rt), f);
-            const float *p = row + k;
+            float p0, p1;
+            const float f = taps(sb, cb, fmaf(jlf[q], M.Bc, rt), p0, p1);
             float w0 = fmaxf(0.0f, fmaf(-f, M.winv, 1.0f));
             float w1 = fmaxf(0.0f, fmaf(f, M.winv, w1c));
-            acc[ry][q] = fmaf(w0, p[0], fmaf(w1, p[1], acc[ry][q]));
+            acc[ry][q] = fmaf(w0, p0, fmaf(w1, p1, acc[ry][q]));
           }
         }
       } else {
@@ -523,13 +543,11 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
           float rt = fmaf(rlf[ry], M.Bs, M.F00);
 #pragma unroll
           for (int q = 0; q < BP2_NQ; ++q) {
-            float xi = fminf(fmaxf(fmaf(jlf[q], M.Bc, rt), lo), hi);
-            float f;
-            int k = dc::floor_frac(xi, f);
-            const float *p = row + k;
+            float p0, p1;
+            const float f = taps(sb, cb, fminf(fmaxf(fmaf(jlf[q], M.Bc, rt), lo), hi), p0, p1);
             float w0 = fmaxf(0.0f, fmaf(-f, M.winv, 1.0f));
             float w1 = fmaxf(0.0f, fmaf(f, M.winv, w1c));
-            acc[ry][q] = fmaf(w0, p[0], fmaf(w1, p[1], acc[ry][q]));
+            acc[ry][q] = fmaf(w0, p0, fmaf(w1, p1, acc[ry][q]));
           }
         }
       }
