@@ -107,6 +107,17 @@ struct MuGroup {
   int pad;
 };
 
+// Line-sum CTAs hold at most DC_LS_MAX_MG angles and DC_LS_MAX_TASKS tasks
+// (angle, chunk of 31 lines).  The group size fills the task table.
+constexpr int DC_LS_MAX_MG = 16;
+constexpr int DC_LS_MAX_TASKS = 256;
+inline int linesum_group_size(int n_s) {
+  int chunks = (n_s - 1 + 30) / 31;
+  if (chunks < 1) chunks = 1;
+  int mg = DC_LS_MAX_TASKS / chunks;
+  return mg < 1 ? 1 : (mg > DC_LS_MAX_MG ? DC_LS_MAX_MG : mg);
+}
+
 }  // namespace dc
 
 // ---------------------------------------------------------------- handle
@@ -133,6 +144,7 @@ struct dc_geometry {
   size_t img_stride;         // floats per padded image  (H * Wp)
   size_t sino_stride;        // floats per padded sinogram (n_mu * NSp)
   int Wp, NSp;               // padded row lengths (multiples of 4)
+  int ls_rb;                 // line-sum band height (32, 16 or 8 rows)
   float *w_img;              // [chunk][H][Wp]
   float *w_sinoA;            // [chunk][n_mu][NSp]
   float *w_sinoB;            // [chunk][n_mu][NSp]

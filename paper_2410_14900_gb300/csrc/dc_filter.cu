@@ -77,14 +77,13 @@ __global__ void __launch_bounds__(256) k_prep(PrepArgs a) {
 // ------------------------------------------------------------- line sums
 enum { M_RAW = 0, M_GRANGEAT = 1, M_FILTER = 2, M_DIFFSTORE = 3, M_ADJ = 4 };
 
-constexpr int LS_THREADS = 256;
+constexpr int LS_THREADS = 512;  // one CTA per SM
 constexpr int LS_WARPS = LS_THREADS / 32;
-constexpr int LS_RB = 16;    // detector rows per band
-constexpr int LS_TPW = 16;   // max (angle, 31-line chunk) tasks per warp
-constexpr int LS_SQ = LS_RB + 1;  // floats per staged sample: odd, so lanes at
-                                  // distinct samples hit distinct banks
+// A band of RB detector rows (32, or 16 / 8 when long detector rows would
+// not fit) is staged with RB + 1 floats per sample: odd, so lanes at distinct
+// samples hit distinct banks.
 constexpr int LS_PJ = 2;     // zero samples staged on each side of a line
-static_assert(LS_RB == 16, "the column-branch copy maps 16 threads to a band");
+static_assert(LS_WARPS * 16 == dc::DC_LS_MAX_TASKS, "task table size");
 
 struct LineArgs {
   const float *img;   // [n][H][Wp]
@@ -119,36 +118,39 @@ struct LineMu {
 // step q sits at fb + q*dxi samples from the band anchor and is interpolated
 // linearly between its two neighbours.  The anchor's byte offset in shared
 // memory is folded with the floor's exponent bits into cb, so one integer
-// multiply-add turns the rounded-down position into the address; NR = LS_RB
+// multiply-add turns the rounded-down position into the address; NR = RB
 // unrolls the band so that the step offset 4q is an immediate (NR = 0 takes
 // nr at run time).  CLAMP pins positions to [lo, hi], inside the zero pads.
-template <bool CLAMP, int NR>
+template <int RB, bool CLAMP, int NR>
 __device__ __forceinline__ float band_sum(const char *sb, unsigned cb, int nr, float fb, float dxi,
                                           float lo, float hi) {
   const float M = 12582912.0f;  // 1.5 * 2^23: x + M rounded down holds floor(x)
+  constexpr int SQ = RB + 1;
   float sum = 0.0f;
 #pragma unroll
-  for (int q = 0; q < (NR ? NR : LS_RB); ++q) {
+  for (int q = 0; q < (NR ? NR : RB); ++q) {
     if (!NR && q >= nr) break;
     float x = fmaf((float)q, dxi, fb);
     if (CLAMP) x = fminf(fmaxf(x, lo), hi);
     const float t = __fadd_rd(x, M);
     const float f = x - (t - M);
-    const unsigned off = __float_as_uint(t) * (unsigned)(LS_SQ * 4) + cb + 4u * q;
+    const unsigned off = __float_as_uint(t) * (unsigned)(SQ * 4) + cb + 4u * q;
     const float g0 = *reinterpret_cast<const float *>(sb + off);
-    const float g1 = *reinterpret_cast<const float *>(sb + off + LS_SQ * 4);
+    const float g1 = *reinterpret_cast<const float *>(sb + off + SQ * 4);
     sum += fmaf(f, g1 - g0, g0);
   }
   return sum;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(LS_THREADS, 2) k_linesum(LineArgs a) {
+template <int MODE, int RB>
+__global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
   constexpr bool DIFF = (MODE != M_RAW);
+  constexpr int LS_RB = RB, LS_SQ = RB + 1;
+  static_assert(LS_THREADS % RB == 0 && RB <= 32, "band copy mapping");
   constexpr int STRIDE_L = DIFF ? 31 : 32;  // lines per task (diff: one overlap)
   extern __shared__ __align__(16) float smem[];
-  __shared__ LineMu lmu[8];
-  __shared__ short2 ttab[LS_TPW * LS_WARPS];
+  __shared__ LineMu lmu[dc::DC_LS_MAX_MG];
+  __shared__ short2 ttab[dc::DC_LS_MAX_TASKS];
 
   const int n = blockIdx.y;
   const dc::MuGroup G = a.groups[blockIdx.x];
@@ -262,10 +264,10 @@ __global__ void __launch_bounds__(LS_THREADS, 2) k_linesum(LineArgs a) {
       const unsigned cb = (unsigned)(st_off + J * LS_SQ * 4) - 0x4B400000u * (unsigned)(LS_SQ * 4);
       float sum;
       if (nr == LS_RB)
-        sum = __all_sync(0xffffffffu, inside) ? band_sum<false, LS_RB>(sb, cb, LS_RB, fb, dxi, lo, hi)
-                                              : band_sum<true, LS_RB>(sb, cb, LS_RB, fb, dxi, lo, hi);
+        sum = __all_sync(0xffffffffu, inside) ? band_sum<RB, false, RB>(sb, cb, RB, fb, dxi, lo, hi)
+                                              : band_sum<RB, true, RB>(sb, cb, RB, fb, dxi, lo, hi);
       else
-        sum = band_sum<true, 0>(sb, cb, nr, fb, dxi, lo, hi);
+        sum = band_sum<RB, true, 0>(sb, cb, nr, fb, dxi, lo, hi);
       const int kl = tk.y + lane;
       if (DIFF) {
         float nb = __shfl_down_sync(0xffffffffu, sum, 1);
@@ -654,12 +656,32 @@ __global__ void k_sino_in(const float *__restrict__ R, const dc::MuRec *__restri
 
 int round4(int x) { return (x + 3) & ~3; }
 
-size_t linesum_smem_for(int H, int W, int mg, int NSp) {
-  return (size_t)(2 * (std::max(H, W) + 2 * LS_PJ) * LS_SQ + mg * NSp) * sizeof(float);
+size_t linesum_smem_for(int H, int W, int mg, int NSp, int rb) {
+  return (size_t)(2 * (std::max(H, W) + 2 * LS_PJ) * (rb + 1) + mg * NSp) * sizeof(float);
+}
+
+// tallest band whose two stages fit the shared-memory budget (0: none)
+int linesum_band_rows(int H, int W, int mg, int NSp) {
+  for (int rb = 32; rb >= 8; rb /= 2)
+    if (linesum_smem_for(H, W, mg, NSp, rb) <= 200 * 1024) return rb;
+  return 0;
 }
 
 size_t linesum_smem(const dc_geometry *g) {
-  return linesum_smem_for(g->d.det_rows, g->d.det_cols, g->mg, g->NSp);
+  return linesum_smem_for(g->d.det_rows, g->d.det_cols, g->mg, g->NSp, g->ls_rb);
+}
+
+template <int MODE, int RB>
+int launch_linesum_rb(dim3 grid, LineArgs &a, size_t sm, cudaStream_t st) {
+  static bool attr_done = false;  // per template instance
+  if (!attr_done) {
+    DC_CUDA(cudaFuncSetAttribute(k_linesum<MODE, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    attr_done = true;
+  }
+  k_linesum<MODE, RB><<<grid, LS_THREADS, sm, st>>>(a);
+  DC_CHECK_LAUNCH("k_linesum");
+  return DC_OK;
 }
 
 size_t bp2d_smem(const dc_geometry *g) {
@@ -669,17 +691,13 @@ size_t bp2d_smem(const dc_geometry *g) {
 template <int MODE>
 int launch_linesum(const dc_geometry *g, LineArgs &a, cudaStream_t st) {
   size_t sm = linesum_smem(g);
-  static bool attr_done = false;  // per template instance
-  if (!attr_done) {
-    DC_CUDA(cudaFuncSetAttribute(k_linesum<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024));
-    attr_done = true;
-  }
   dim3 grid(g->n_groups, a.n_img);
   dc::ProfScope ps(dc::KID_LINESUM, st);
-  k_linesum<MODE><<<grid, LS_THREADS, sm, st>>>(a);
-  DC_CHECK_LAUNCH("k_linesum");
-  return DC_OK;
+  switch (g->ls_rb) {
+    case 32: return launch_linesum_rb<MODE, 32>(grid, a, sm, st);
+    case 16: return launch_linesum_rb<MODE, 16>(grid, a, sm, st);
+    default: return launch_linesum_rb<MODE, 8>(grid, a, sm, st);
+  }
 }
 
 int launch_bp2d(const dc_geometry *g, BP2Args &a, cudaStream_t st) {
@@ -820,7 +838,8 @@ int alloc_workspace(dc_geometry *g) {
   g->chunk_images = ci;
   g->chunk_capacity = ci;
   g->bp_nz = 32;
-  if (linesum_smem(g) > 200 * 1024 || bp2d_smem(g) > 200 * 1024)
+  g->ls_rb = linesum_band_rows(d.det_rows, d.det_cols, g->mg, g->NSp);
+  if (g->ls_rb == 0 || bp2d_smem(g) > 200 * 1024)
     return fail(DC_ERR_UNSUPPORTED, "detector or sinogram rows too long for shared memory");
   DC_CUDA(dmalloc((void **)&g->w_img, sizeof(float) * g->img_stride * ci));
   DC_CUDA(dmalloc((void **)&g->w_sinoA, sizeof(float) * g->sino_stride * ci));
@@ -1102,11 +1121,11 @@ extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, do
                                     std::to_string(W) + " image needs " +
                                     std::to_string(per_img) + " bytes of work area; the fixed "
                                     "maximum is " + std::to_string(cap) + " bytes");
-  int chunks = (n_s - 1 + 30) / 31;
-  int mg = std::max(1, std::min(8, (16 * 8) / std::max(1, chunks)));
-  size_t smem = linesum_smem_for(H, W, mg, NSp);
-  if (smem > 200 * 1024)
+  const int mg = dc::linesum_group_size(n_s);
+  const int rb = linesum_band_rows(H, W, mg, NSp);
+  if (rb == 0)
     return dc::fail(DC_ERR_UNSUPPORTED, "dc_radon2d_noalloc: rows too long for shared memory");
+  const size_t smem = linesum_smem_for(H, W, mg, NSp, rb);
 
   int dev = 0;
   DC_CUDA(cudaGetDevice(&dev));
@@ -1144,8 +1163,6 @@ extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, do
   for (int m = 0; m < n_mu; ++m) ((4 * m <= n_mu) || (4 * m >= 3 * n_mu) ? nb0 : nb1) += 1;
   const int n_groups_h = (nb0 + mg - 1) / mg + (nb1 + mg - 1) / mg;
 
-  DC_CUDA(cudaFuncSetAttribute(k_linesum<M_RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               200 * 1024));
   const int per_chunk = (int)std::min<size_t>(cap / per_img, 65535);
   float *img_w = work;
   for (int n0 = 0; n0 < n_img; n0 += per_chunk) {
@@ -1198,8 +1215,10 @@ extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, do
     dim3 grid(n_groups_h, nc);
     {
       dc::ProfScope ps(dc::KID_LINESUM, st);
-      k_linesum<M_RAW><<<grid, LS_THREADS, smem, st>>>(a);
-      DC_CHECK_LAUNCH("k_linesum");
+      int rc = rb == 32 ? launch_linesum_rb<M_RAW, 32>(grid, a, smem, st)
+               : rb == 16 ? launch_linesum_rb<M_RAW, 16>(grid, a, smem, st)
+                          : launch_linesum_rb<M_RAW, 8>(grid, a, smem, st);
+      if (rc != DC_OK) return rc;
     }
   }
   return DC_OK;

@@ -187,13 +187,7 @@ int build_mu_tables(dc_geometry *g) {
     mu[m] = make_mu_rec(m, n_mu, d.pitch, d.ds);
     (rows ? b0 : b1).push_back(m);
   }
-  // angles per group: keep the per-warp task count of the line-sum kernel
-  // (ceil(n_s/31) chunks per angle, 8 warps) at or below 16.
-  int chunks = (d.n_s - 1 + 30) / 31;
-  if (chunks < 1) chunks = 1;
-  int mg = (16 * 8) / chunks;
-  if (mg > 8) mg = 8;
-  if (mg < 1) mg = 1;
+  const int mg = linesum_group_size(d.n_s);
   g->mg = mg;
   std::vector<int> order;
   std::vector<MuGroup> groups;
