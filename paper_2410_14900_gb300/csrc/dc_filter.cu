@@ -408,9 +408,14 @@ struct BP2Args {
   unsigned *err;
 };
 
+// per-angle constants of one tile: the s-bin position of pixel (j0 + jl,
+// r0 + rl) is I00 + F00 + jl*Bc + rl*Bs (I00 integer, F00 in [0, 1))
 struct BPMu {
-  float F00, I00, Bc, Bs, winv, pad0, pad1;
-  int i00;  // I00 as an integer
+  float F00, Bc, Bs, winv;  // winv: slope of the Joseph hat in s-bins
+  float w1c, lo, hi;        // 1 - winv; positions relative to I00 clamp to [lo, hi]
+  unsigned cbase;           // byte offset of s-bin I00 in its stage, minus the floor's exponent bits
+  int fast;                 // positions stay inside (lo, hi) over the tile: no clamp
+  int pad0, pad1, pad2;
 };
 
 // the two sinogram taps around s-bin position x (relative to a row anchor
@@ -459,12 +464,7 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
       dc::bulk_g2s(smem + (c & 1) * stage_sz + (size_t)q * rstride + PADL, src + (size_t)(m0 + q) * a.NSp,
                    (unsigned)(a.NSp * 4), bar);
   };
-  // per-angle constants (FP64 once per CTA and angle): xi(j, r) = position of
-  // pixel (j, r) on the s grid, in s-bin units; xi(j0+jl, r0+rl) =
-  // I00 + F00 + jl*Bc + rl*Bs
-  // per-angle constants of this tile (FP32 from exact splits): the s-bin
-  // position of pixel (j0 + jl, r0 + rl) is I00 + F00 + jl*Bc + rl*Bs; pad0
-  // flags angles whose positions stay inside the clamp range over the tile
+  // per-angle constants of this tile, from exact float splits of the origin
   auto angle_consts = [&](int c) {
     int mi = threadIdx.x;
     int m = c * BP2_MC + mi;
@@ -476,19 +476,21 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
       float ti = floorf(t);
       float F = Q.xof + (t - ti) + fmaf(fj0, R.bc_lo, fr0 * R.bs_lo);
       float Fi = floorf(F);
+      const float I00 = Q.xoi + ti + Fi;
       BPMu M;
-      M.I00 = Q.xoi + ti + Fi;
       M.F00 = F - Fi;
       M.Bc = R.bc_hi + R.bc_lo;
       M.Bs = R.bs_hi + R.bs_lo;
       M.winv = R.winv;
+      M.w1c = 1.0f - R.winv;
+      M.lo = -1.0f - I00;
+      M.hi = (float)a.n_s - I00;
+      M.cbase = (unsigned)((mi * rstride + PADL + (int)I00) * 4) - 4u * 0x4B400000u;
       float ex = (float)(BP2_TX - 1) * M.Bc, ey = (float)(BP2_TY - 1) * M.Bs;
       float xmin = M.F00 + fminf(ex, 0.0f) + fminf(ey, 0.0f);
       float xmax = M.F00 + fmaxf(ex, 0.0f) + fmaxf(ey, 0.0f);
-      M.pad0 = (xmin >= -1.0f - M.I00 + 0.01f && xmax <= (float)a.n_s - M.I00 - 0.01f) ? 1.0f
-                                                                                          : 0.0f;
-      M.pad1 = 0.0f;
-      M.i00 = (int)M.I00;
+      M.fast = (xmin >= M.lo + 0.01f && xmax <= M.hi - 0.01f) ? 1 : 0;
+      M.pad0 = M.pad1 = M.pad2 = 0;
       bmu[c & 1][mi] = M;
     }
   };
@@ -518,14 +520,13 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
       ok = false;
       break;
     }
-    const int st_off = (c & 1) * stage_sz;  // floats
+    const unsigned st_off = (unsigned)((c & 1) * stage_sz * 4);  // bytes
     int nm = min(BP2_MC, a.n_mu - c * BP2_MC);
+#pragma unroll 2
     for (int mi = 0; mi < nm; ++mi) {
       const BPMu M = bmu[c & 1][mi];
-      // byte offset of s-bin I00 of this angle's row, minus the floor's exponent bits
-      const unsigned cb = (unsigned)((st_off + mi * rstride + PADL + M.i00) * 4) - 4u * 0x4B400000u;
-      float w1c = 1.0f - M.winv;
-      if (M.pad0 != 0.0f) {
+      const unsigned cb = M.cbase + st_off;
+      if (M.fast) {
 #pragma unroll
         for (int ry = 0; ry < BP2_RY; ++ry) {
           float rt = fmaf(rlf[ry], M.Bs, M.F00);
@@ -534,21 +535,21 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
             float p0, p1;
             const float f = taps(sb, cb, fmaf(jlf[q], M.Bc, rt), p0, p1);
             float w0 = fmaxf(0.0f, fmaf(-f, M.winv, 1.0f));
-            float w1 = fmaxf(0.0f, fmaf(f, M.winv, w1c));
+            float w1 = fmaxf(0.0f, fmaf(f, M.winv, M.w1c));
             acc[ry][q] = fmaf(w0, p0, fmaf(w1, p1, acc[ry][q]));
           }
         }
       } else {
-        float lo = -1.0f - M.I00, hi = (float)a.n_s - M.I00;
 #pragma unroll
         for (int ry = 0; ry < BP2_RY; ++ry) {
           float rt = fmaf(rlf[ry], M.Bs, M.F00);
 #pragma unroll
           for (int q = 0; q < BP2_NQ; ++q) {
             float p0, p1;
-            const float f = taps(sb, cb, fminf(fmaxf(fmaf(jlf[q], M.Bc, rt), lo), hi), p0, p1);
+            const float f =
+                taps(sb, cb, fminf(fmaxf(fmaf(jlf[q], M.Bc, rt), M.lo), M.hi), p0, p1);
             float w0 = fmaxf(0.0f, fmaf(-f, M.winv, 1.0f));
-            float w1 = fmaxf(0.0f, fmaf(f, M.winv, w1c));
+            float w1 = fmaxf(0.0f, fmaf(f, M.winv, M.w1c));
             acc[ry][q] = fmaf(w0, p0, fmaf(w1, p1, acc[ry][q]));
           }
         }
