@@ -81,8 +81,10 @@ constexpr int LS_THREADS = 512;  // one CTA per SM
 constexpr int LS_WARPS = LS_THREADS / 32;
 // A band of RB detector rows (32, or 16 / 8 when long detector rows would
 // not fit) is staged with RB + 1 floats per sample: odd, so lanes at distinct
-// samples hit distinct banks.
-constexpr int LS_PJ = 2;     // zero samples staged on each side of a line
+// samples hit distinct banks.  RB + 1 zero samples pad each side: a line that
+// meets the detector anywhere in a band moves less than RB samples (slope at
+// most 1) over the band, so its taps never leave the stage and need no clamp.
+constexpr int LS_SMEM_BUDGET = 225 * 1024;  // one CTA per SM
 static_assert(LS_WARPS * 16 == dc::DC_LS_MAX_TASKS, "task table size");
 
 struct LineArgs {
@@ -116,22 +118,21 @@ struct LineMu {
 
 // Joseph sum of one line over the nr steps of a staged band: the sample at
 // step q sits at fb + q*dxi samples from the band anchor and is interpolated
-// linearly between its two neighbours.  The anchor's byte offset in shared
-// memory is folded with the floor's exponent bits into cb, so one integer
-// multiply-add turns the rounded-down position into the address; NR = RB
-// unrolls the band so that the step offset 4q is an immediate (NR = 0 takes
-// nr at run time).  CLAMP pins positions to [lo, hi], inside the zero pads.
-template <int RB, bool CLAMP, int NR>
-__device__ __forceinline__ float band_sum(const char *sb, unsigned cb, int nr, float fb, float dxi,
-                                          float lo, float hi) {
+// linearly between its two neighbours (zero pads outside the detector).  The
+// anchor's byte offset in shared memory is folded with the floor's exponent
+// bits into cb, so one integer multiply-add turns the rounded-down position
+// into the address; NR = RB unrolls the band so that the step offset 4q is an
+// immediate (NR = 0 takes nr at run time).
+template <int RB, int NR>
+__device__ __forceinline__ float band_sum(const char *sb, unsigned cb, int nr, float fb,
+                                          float dxi) {
   const float M = 12582912.0f;  // 1.5 * 2^23: x + M rounded down holds floor(x)
   constexpr int SQ = RB + 1;
   float sum = 0.0f;
 #pragma unroll
   for (int q = 0; q < (NR ? NR : RB); ++q) {
     if (!NR && q >= nr) break;
-    float x = fmaf((float)q, dxi, fb);
-    if (CLAMP) x = fminf(fmaxf(x, lo), hi);
+    const float x = fmaf((float)q, dxi, fb);
     const float t = __fadd_rd(x, M);
     const float f = x - (t - M);
     const unsigned off = __float_as_uint(t) * (unsigned)(SQ * 4) + cb + 4u * q;
@@ -145,7 +146,7 @@ __device__ __forceinline__ float band_sum(const char *sb, unsigned cb, int nr, f
 template <int MODE, int RB>
 __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
   constexpr bool DIFF = (MODE != M_RAW);
-  constexpr int LS_RB = RB, LS_SQ = RB + 1;
+  constexpr int LS_RB = RB, LS_SQ = RB + 1, LS_PJ = RB + 1;
   static_assert(LS_THREADS % RB == 0 && RB <= 32, "band copy mapping");
   constexpr int STRIDE_L = DIFF ? 31 : 32;  // lines per task (diff: one overlap)
   extern __shared__ __align__(16) float smem[];
@@ -254,20 +255,19 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
       const int J = (int)L.b0i + (int)t1i + (int)thi + (int)fri;
       const float fb = fr - fri;
       const float dxi = L.dxi;
-      float lo = (float)(-1 - J), hi = (float)(len - J);
-      float xa = fb, xb = fmaf((float)(nr - 1), dxi, fb);
-      float xmin = fminf(xa, xb), xmax = fmaxf(xa, xb);
-      bool outside = (xmax <= lo) || (xmin >= hi);
+      // the lane's samples lie in [-1, len] somewhere in the band, or nowhere
+      const float lo = (float)(-1 - J), hi = (float)(len - J);
+      const float xa = fb, xb = fmaf((float)(nr - 1), dxi, fb);
+      const bool outside = (fmaxf(xa, xb) <= lo) || (fminf(xa, xb) >= hi);
       if (__all_sync(0xffffffffu, outside)) continue;  // the band misses these lines
-      bool inside = (xmin >= lo + 1.0f) && (xmax <= hi - 1.0f);
-      // byte offset of sample J of this stage, minus the floor's exponent bits
-      const unsigned cb = (unsigned)(st_off + J * LS_SQ * 4) - 0x4B400000u * (unsigned)(LS_SQ * 4);
-      float sum;
-      if (nr == LS_RB)
-        sum = __all_sync(0xffffffffu, inside) ? band_sum<RB, false, RB>(sb, cb, RB, fb, dxi, lo, hi)
-                                              : band_sum<RB, true, RB>(sb, cb, RB, fb, dxi, lo, hi);
-      else
-        sum = band_sum<RB, true, 0>(sb, cb, nr, fb, dxi, lo, hi);
+      float sum = 0.0f;
+      if (!outside) {
+        // byte offset of sample J of this stage, minus the floor's exponent bits
+        const unsigned cb =
+            (unsigned)(st_off + J * LS_SQ * 4) - 0x4B400000u * (unsigned)(LS_SQ * 4);
+        sum = (nr == RB) ? band_sum<RB, RB>(sb, cb, RB, fb, dxi)
+                         : band_sum<RB, 0>(sb, cb, nr, fb, dxi);
+      }
       const int kl = tk.y + lane;
       if (DIFF) {
         float nb = __shfl_down_sync(0xffffffffu, sum, 1);
@@ -658,13 +658,13 @@ __global__ void k_sino_in(const float *__restrict__ R, const dc::MuRec *__restri
 int round4(int x) { return (x + 3) & ~3; }
 
 size_t linesum_smem_for(int H, int W, int mg, int NSp, int rb) {
-  return (size_t)(2 * (std::max(H, W) + 2 * LS_PJ) * (rb + 1) + mg * NSp) * sizeof(float);
+  return (size_t)(2 * (std::max(H, W) + 2 * (rb + 1)) * (rb + 1) + mg * NSp) * sizeof(float);
 }
 
 // tallest band whose two stages fit the shared-memory budget (0: none)
 int linesum_band_rows(int H, int W, int mg, int NSp) {
   for (int rb = 32; rb >= 8; rb /= 2)
-    if (linesum_smem_for(H, W, mg, NSp, rb) <= 200 * 1024) return rb;
+    if (linesum_smem_for(H, W, mg, NSp, rb) <= LS_SMEM_BUDGET) return rb;
   return 0;
 }
 
@@ -677,7 +677,7 @@ int launch_linesum_rb(dim3 grid, LineArgs &a, size_t sm, cudaStream_t st) {
   static bool attr_done = false;  // per template instance
   if (!attr_done) {
     DC_CUDA(cudaFuncSetAttribute(k_linesum<MODE, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024));
+                                 LS_SMEM_BUDGET));
     attr_done = true;
   }
   k_linesum<MODE, RB><<<grid, LS_THREADS, sm, st>>>(a);
