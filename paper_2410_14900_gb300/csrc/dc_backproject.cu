@@ -284,8 +284,13 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
   const char *sb = reinterpret_cast<const char *>(dsm);
 
   const int tid = threadIdx.y * TB_TX + threadIdx.x;
-  const int ix = bxi * TB_TX + threadIdx.x;
-  const int iy = byi * TB_TY + threadIdx.y;
+  // each half-warp (the lanes of one 64-bit shared-memory wavefront) takes a
+  // 4 x 4 patch of voxel columns: its taps span a few columns and at most two
+  // rows of the pair tile, which the row stride maps to distinct banks
+  static_assert(TB_TX == 16 && TB_TY == 16, "4 x 4 patches of a 16 x 16 box");
+  const int hw = tid >> 4, l16 = tid & 15;
+  const int ix = bxi * TB_TX + ((hw & 3) << 2) + (l16 & 3);
+  const int iy = byi * TB_TY + ((hw >> 2) << 2) + (l16 >> 2);
   const int zblocks = (a.nz + NZ - 1) / NZ;
   const int b = bzi / zblocks;
   const int z0 = (bzi % zblocks) * NZ;
