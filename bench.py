@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-paper-shape", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched-orbits measurement (for profiling)")
     ap.add_argument("--train-only", action="store_true",
@@ -326,6 +327,56 @@ def batched_measure(args, dev, L):
     return out
 
 
+def paper_shape_measure(args, dev, L):
+    """The paper's own workload shape (Tables 1-2: 400 views of a tilted
+    sinusoid, 620x480 detector at 0.616 mm, 360 x 785 planes, 128x512x512
+    volume at 0.25 mm), FP32, timed like the headline workload."""
+    import torch
+    from paper_2410_14900_gb300 import api, synth, tune
+
+    w = synth.workload("paper400")
+    geom = api.Geometry(w.desc_dict(), w.matrices(), w.orbit.vdl)
+    tuned = tune.autotune(geom, "f32", chunks=(8, 12, 16, 20, 25), nzs=(16, 32))
+    g = synth.project_phantom(w.phantoms()[0], w.orbit, w.det_rows, w.det_cols, w.pitch,
+                              device=dev, dtype=torch.float32)[None].contiguous()
+    gF = torch.empty_like(g)
+    vol = torch.empty((1,) + geom.vol_shape, device=dev)
+
+    def step():
+        api.dc_filter(geom, g, None, "f32", out=gF)
+        api.dc_backproject(geom, gF, None, out=vol)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    L.dc_profile_enable(1)
+    L.dc_profile_collect(None, None, 0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_k = np.zeros(16, dtype=np.float64)
+    cnt_k = np.zeros(16, dtype=np.uint64)
+    nk = L.dc_profile_collect(ms_k.ctypes.data, cnt_k.ctypes.data, 16)
+    L.dc_profile_enable(0)
+    kern = {L.dc_profile_kernel_name(i).decode(): float(ms_k[i]) / args.steps
+            for i in range(nk) if cnt_k[i]}
+    api.dc_sync_status(geom)
+    geom.close()
+    bp = kern.get("k_bp3d", 0.0)
+    return {"workload": w.name, "orbit": w.orbit.kind, "views": w.n_views,
+            "detector": [w.det_rows, w.det_cols], "planes": [w.n_mu, w.n_s],
+            "volume": list(w.vol_shape), "ms_per_volume": e0.elapsed_time(e1) / args.steps,
+            "filter_ms": sum(kern.get(k, 0.0) for k in ("k_prep", "k_linesum", "k_bp2d")),
+            "backproject_ms": bp,
+            "bp_gups": w.n_views * float(np.prod(w.vol_shape)) / (bp * 1e-3) / 1e9 if bp else None,
+            "tuning": {k: tuned[k] for k in ("chunk_images", "bp_nz")}}
+
+
 # --------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -488,6 +539,10 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_batched:
         batched = batched_measure(args, dev, L)
 
+    paper_shape = None
+    if not args.no_paper_shape:
+        paper_shape = paper_shape_measure(args, dev, L)
+
     train = None
     if not args.no_train:
         del gF, vol
@@ -516,7 +571,7 @@ def run_ours(args, rank, world, local_rank):
                            "tuning": {k: tuned[k] for k in ("chunk_images", "bp_nz")},
                            "l2": "inputs larger than L2 (g 390 MB, f 537 MB), no flush"},
                 "roofline": roof, "breakdown": breakdown, "forms": forms, "train_step": train,
-                "batched": batched,
+                "batched": batched, "paper_shape": paper_shape,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(n_launch),
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -49,6 +49,16 @@ def arc_open(B: int = 1) -> Case:
     return Case("arc_open", desc, synth.projection_matrices(o, H, W, p), None, o, B)
 
 
+def random_nn(B: int = 1) -> Case:
+    """The random nearest-neighbour orbit (open, finite-difference tangents)."""
+    o = synth.random_nn_orbit(30, seed=3)
+    H, W, p = 40, 48, 1.6
+    desc = dict(n_views=o.n_views, det_rows=H, det_cols=W, n_mu=36, n_s=44, pitch=p, ds=p,
+                vol_x=24, vol_y=24, vol_z=20, voxel=(1.0, 1.0, 1.0),
+                vol_center=(0.0, 0.0, 0.0), closed_orbit=0)
+    return Case("random_nn", desc, synth.projection_matrices(o, H, W, p), o.vdl, o, B)
+
+
 def phantom_projections(case: Case, seed: int = 0, n: int = 8) -> np.ndarray:
     """[B,V,H,W] exact line integrals of seeded ellipsoid phantoms (FP64)."""
     d = case.desc

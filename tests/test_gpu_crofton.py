@@ -7,16 +7,17 @@ import torch
 from oracle import oracle as orc
 from paper_2410_14900_gb300 import api, synth
 
-from cases import arc_open, circle64, phantom_projections, ragged, rel_l2
+from cases import arc_open, circle64, phantom_projections, ragged, random_nn, rel_l2
 
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("name", ["circle64", "ragged", "arc_open"])
+@pytest.mark.parametrize("name", ["circle64", "ragged", "arc_open", "random_nn"])
 @pytest.mark.parametrize("m,taper", [(2, 3), (1, 0), (0, 0)])
 def test_crofton_weights_match_oracle(name, m, taper):
-    case = {"circle64": circle64, "ragged": ragged, "arc_open": arc_open}[name]()
-    segs = [(0, True), (20, False)] if name == "arc_open" else None
+    case = {"circle64": circle64, "ragged": ragged, "arc_open": arc_open,
+            "random_nn": random_nn}[name]()
+    segs = {"arc_open": [(0, True), (20, False)], "random_nn": [(0, False)]}.get(name)
     gg = api.Geometry(case.desc, case.P, case.vdl)
     og = orc.Geometry(case.desc, case.P, case.vdl)
     W = api.dc_crofton_weights(gg, segs, m=m, taper=taper).double().cpu().numpy()

@@ -12,11 +12,12 @@ from oracle import oracle as orc
 from paper_2410_14900_gb300 import api
 from paper_2410_14900_gb300 import _lib as L
 
-from cases import arc_open, circle64, phantom_projections, ragged, random_weights, rel_l2
+from cases import (arc_open, circle64, phantom_projections, ragged, random_nn, random_weights,
+                   rel_l2)
 
 pytestmark = pytest.mark.gpu
 
-CASES = {"circle64": circle64, "ragged": ragged, "arc_open": arc_open}
+CASES = {"circle64": circle64, "ragged": ragged, "arc_open": arc_open, "random_nn": random_nn}
 
 
 def _setup(case):

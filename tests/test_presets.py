@@ -46,6 +46,26 @@ def test_orbits_have_the_stated_shapes():
         assert np.abs(fd - o.vdl).max() < 2e-3 * np.abs(o.vdl).max()
 
 
+def test_random_nearest_neighbour_orbit():
+    """Sec. 4.4's random orbit: points on the sphere band of +-10 degrees,
+    chained by nearest neighbour, tangents from central differences."""
+    o = synth.random_nn_orbit(120, seed=4)
+    a = o.sources
+    assert o.n_views == 120 and not o.closed
+    assert np.allclose(np.linalg.norm(a, axis=1), synth.SID_MM)
+    assert np.degrees(np.abs(np.arcsin(a[:, 2] / synth.SID_MM))).max() <= 10.0 + 1e-9
+    for i in range(len(a) - 2):   # every next point is the nearest of the rest
+        d = np.sum((a[i + 1:] - a[i]) ** 2, axis=1)
+        assert d[0] == d.min()
+    assert np.allclose(o.vdl[1:-1], 0.5 * (a[2:] - a[:-2]))
+    assert np.allclose(o.vdl[0], a[1] - a[0]) and np.allclose(o.vdl[-1], a[-1] - a[-2])
+    # detector frame: orthonormal, principal ray through the isocentre
+    for lx, ly, lz, ai in zip(o.lx, o.ly, o.lz, a):
+        F = np.stack([lx, ly, lz])
+        assert np.allclose(F @ F.T, np.eye(3), atol=1e-12)
+        assert np.allclose(lz, ai / np.linalg.norm(ai))
+
+
 def test_phantom_line_integrals_match_quadrature():
     rng = np.random.default_rng(0)
     for kind in ("ellipsoid", "gauss"):
