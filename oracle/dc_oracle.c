@@ -666,3 +666,78 @@ void orc_crofton_weights(int V, int n_mu, int n_s, double ds, const double *geo,
   free(cj);
   free(segof);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian smoothing of the learned redundancy weight (Sec. 3.1)            */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The paper smooths the learned weight with a Gaussian filter layer (sigma
+ * 20, kernel size 121) without stating the axes or the boundary.  Reading
+ * used here: per view, a separable filter along mu and along s over the
+ * valid half-grid entries k < n_s - 1 (the unused entry n_s - 1 passes
+ * through); taps exp(-t^2 / (2 sigma^2)) for |t| <= radius, normalised to
+ * unit sum; mirror extension at both ends of a line (index -1 reads index 1,
+ * index n reads n - 2, repeated for lines shorter than the radius).
+ */
+static int mirror_index(int p, int n) {
+  if (n == 1) return 0;
+  int T = 2 * (n - 1);
+  p %= T;
+  if (p < 0) p += T;
+  return p < n ? p : T - p;
+}
+
+static void gauss_taps(double sigma, int radius, double *w) {
+  double sum = 0.0;
+  for (int t = -radius; t <= radius; ++t) {
+    w[t + radius] = exp(-0.5 * (double)t * t / (sigma * sigma));
+    sum += w[t + radius];
+  }
+  for (int t = 0; t <= 2 * radius; ++t) w[t] /= sum;
+}
+
+/* y = G x along one line of n elements spaced `stride` apart */
+static void smooth_line(const double *x, double *y, int n, size_t stride, const double *w,
+                        int radius) {
+  for (int i = 0; i < n; ++i) {
+    double acc = 0.0;
+    for (int t = -radius; t <= radius; ++t) acc += w[t + radius] * x[mirror_index(i + t, n) * stride];
+    y[i * stride] = acc;
+  }
+}
+
+/* x = G^T y along one line: the literal transpose (scatter) of smooth_line */
+static void smooth_line_T(const double *y, double *x, int n, size_t stride, const double *w,
+                          int radius) {
+  for (int i = 0; i < n; ++i) x[i * stride] = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int t = -radius; t <= radius; ++t) x[mirror_index(i + t, n) * stride] += w[t + radius] * y[i * stride];
+}
+
+/* adjoint = 0: out = G_s G_mu in;  adjoint = 1: out = G_mu^T G_s^T in.
+ * in, out: [V][n_mu][n_s] (may not alias). */
+void orc_gauss_smooth(int V, int n_mu, int n_s, double sigma, int radius, int adjoint,
+                      const double *in, double *out) {
+  double *w = malloc(sizeof(double) * (2 * radius + 1));
+  gauss_taps(sigma, radius, w);
+  size_t nv = (size_t)n_mu * n_s;
+  double *tmp = malloc(sizeof(double) * nv * V);
+  memcpy(out, in, sizeof(double) * nv * V);
+  memcpy(tmp, in, sizeof(double) * nv * V);
+  int ns1 = n_s - 1;
+#pragma omp parallel for schedule(static)
+  for (int v = 0; v < V; ++v) {
+    const double *x = in + v * nv;
+    double *t = tmp + v * nv, *y = out + v * nv;
+    if (!adjoint) {
+      for (int k = 0; k < ns1; ++k) smooth_line(x + k, t + k, n_mu, (size_t)n_s, w, radius);
+      for (int m = 0; m < n_mu; ++m) smooth_line(t + (size_t)m * n_s, y + (size_t)m * n_s, ns1, 1, w, radius);
+    } else {
+      for (int m = 0; m < n_mu; ++m) smooth_line_T(x + (size_t)m * n_s, t + (size_t)m * n_s, ns1, 1, w, radius);
+      for (int k = 0; k < ns1; ++k) smooth_line_T(t + k, y + k, n_mu, (size_t)n_s, w, radius);
+    }
+  }
+  free(tmp);
+  free(w);
+}

@@ -320,6 +320,19 @@ def crofton_weights(geom: Geometry, segments=None, m: int = 2, taper: int = 5) -
     return out
 
 
+def gauss_smooth(W: np.ndarray, sigma: float = 20.0, radius: int = 60,
+                 adjoint: bool = False) -> np.ndarray:
+    """The Gaussian filter layer on the redundancy weight (Sec. 3.1): per
+    view, separable along mu and s over the valid entries k < n_s - 1, unit-sum
+    taps, mirror ends.  adjoint=True applies the transpose."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    V, n_mu, n_s = W.shape
+    out = np.empty_like(W)
+    lib().orc_gauss_smooth(_ci(V), _ci(n_mu), _ci(n_s), _cd(sigma), _ci(radius),
+                           _ci(int(bool(adjoint))), _p(W), _p(out))
+    return out
+
+
 def reconstruct(geom: Geometry, g: np.ndarray, Wred=None, relu=False) -> np.ndarray:
     """Eq. 12: f = A3d^T w_d A2d^T D w_red w_sino D A2d w_cos g."""
     return backproject(geom, filter(geom, g, Wred), relu=relu)

@@ -585,3 +585,39 @@ def test_crofton_weights_reconstruct_circle_plus_arc_off_midplane():
         err[name] = np.linalg.norm((f - gt)[roi]) / np.linalg.norm(gt[roi])
     assert err["crofton"] < 0.04, err
     assert err["half"] > 4 * err["crofton"], err
+
+
+# ------------------------------------------------ Gaussian smoothing of W
+def test_gauss_smooth_is_scipys_mirror_filter():
+    """Separable 121-tap Gaussian (sigma 20) with mirror ends: the same as
+    scipy's gaussian_filter1d(mode='mirror', truncate=3) along mu and s."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(21)
+    W = rng.normal(size=(3, 150, 97))
+    got = orc.gauss_smooth(W, 20.0, 60)
+    ref = W.copy()
+    v = ndimage.gaussian_filter1d(W[:, :, :-1], 20.0, axis=1, mode="mirror", truncate=3.0)
+    ref[:, :, :-1] = ndimage.gaussian_filter1d(v, 20.0, axis=2, mode="mirror", truncate=3.0)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(W).max())
+    np.testing.assert_array_equal(got[:, :, -1], W[:, :, -1])  # unused entry passes
+
+
+def test_gauss_smooth_closed_forms_and_adjoint():
+    # constants are kept (unit-sum taps); a delta far from the ends spreads
+    # into the sampled Gaussian profile; short lines mirror repeatedly
+    W = np.full((2, 40, 33), 0.7)
+    np.testing.assert_allclose(orc.gauss_smooth(W, 20.0, 60), W, atol=1e-14)
+    D = np.zeros((1, 301, 302))
+    D[0, 150, 150] = 1.0
+    S = orc.gauss_smooth(D, 5.0, 15)
+    t = np.arange(-15, 16)
+    g = np.exp(-0.5 * t ** 2 / 25.0)
+    g /= g.sum()
+    np.testing.assert_allclose(S[0, 135:166, 135:166], np.outer(g, g), atol=1e-15)
+    assert abs(S.sum() - 1.0) < 1e-12
+    rng = np.random.default_rng(22)
+    x = rng.normal(size=(2, 37, 29))
+    y = rng.normal(size=(2, 37, 29))
+    lhs = np.sum(orc.gauss_smooth(x, 20.0, 60) * y)
+    rhs = np.sum(x * orc.gauss_smooth(y, 20.0, 60, adjoint=True))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
