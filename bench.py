@@ -224,7 +224,8 @@ def run_reference(args, rank, world):
 def train_step_measure(args, dev, L, world):
     """Forward + backward + AdamW step of the learnable redundancy weights:
     sinusoidal orbit, 360 views, 256^2 detector, 256^3 volume, batch of 4
-    seeded phantoms, MSE against the phantom volumes, ReLU output."""
+    seeded phantoms, the Gaussian filter layer on W (sigma 20, kernel 121),
+    MSE against the phantom volumes, ReLU output."""
     import torch
     from paper_2410_14900_gb300 import api, synth
     from paper_2410_14900_gb300.autograd import DefriseClackNet
@@ -235,7 +236,7 @@ def train_step_measure(args, dev, L, world):
     g = torch.stack([synth.project_phantom(b, w.orbit, w.det_rows, w.det_cols, w.pitch,
                                            device=dev, dtype=torch.float32) for b in phs])
     tgt = torch.stack([synth.phantom_volume(b, w.vol_shape, w.voxel, device=dev) for b in phs])
-    net = DefriseClackNet(geom, init=0.5, relu=True, device=dev)
+    net = DefriseClackNet(geom, init=0.5, relu=True, device=dev, smooth=(20.0, 60))
     opt = torch.optim.AdamW(net.parameters(), lr=1e-3)
 
     def step():
@@ -270,7 +271,8 @@ def train_step_measure(args, dev, L, world):
     return {"workload": w.name, "ms_per_step": ms, "batch": w.batch,
             "views": w.n_views, "volume": list(w.vol_shape), "weights": [w.n_views, w.n_mu, w.n_s],
             "loss": float(loss.item()), "kernel_ms_per_step": kernels,
-            "optimizer": "AdamW (lr 1e-3)", "note": "forward + backward + optimizer step"}
+            "optimizer": "AdamW (lr 1e-3)", "smooth": [20.0, 60],
+            "note": "forward + backward + optimizer step"}
 
 
 # --------------------------------------------------------------- batched

@@ -209,6 +209,24 @@ int dc_crofton_weights(const dc_geometry *geom, int n_seg, const int *seg_start,
                        const int *seg_closed, int m, int taper, float *W, void *stream);
 
 /*
+ * dc_gauss_smooth -- the Gaussian filter layer the paper places after the
+ * learned redundancy weight (Sec. 3.1: sigma 20, kernel size 121, i.e.
+ * radius 60), or its transpose for the reverse mode.  Per view, W[mu][k] is
+ * filtered along mu and along s over the valid entries k < n_s - 1; entry
+ * n_s - 1 is copied through.  Taps exp(-t^2/(2 sigma^2)) for |t| <= radius,
+ * normalised to unit sum; each line is extended by mirroring about its end
+ * samples (index -1 reads 1, index n reads n - 2).
+ *   in, out : device, [V][n_mu][n_s] FP32; out is written.
+ *   work    : device scratch of V*n_mu*n_s floats, owned by the caller.
+ *   adjoint : 0 applies the filter, 1 its transpose.
+ * in, out and work must be distinct.  DC_ERR_ARG for bad sizes, sigma <= 0
+ * or radius outside [0, 1024]; DC_ERR_UNSUPPORTED when a line and its halo
+ * do not fit in shared memory (n_mu or n_s + 3 radius beyond ~25000).
+ */
+int dc_gauss_smooth(int V, int n_mu, int n_s, float sigma, int radius, int adjoint,
+                    const float *in, float *out, float *work, void *stream);
+
+/*
  * Batched reconstruction of several problems (orbits with uneven view
  * counts, detectors and volumes): Eq. 12 for each, with the backprojection
  * of all problems done by one persistent kernel that takes (problem, voxel

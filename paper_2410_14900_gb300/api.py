@@ -250,6 +250,25 @@ def dc_crofton_weights(geom: Geometry, segments=None, m: int = 2, taper: int = 5
     return W
 
 
+def dc_gauss_smooth(W: torch.Tensor, sigma: float = 20.0, radius: int = 60,
+                    adjoint: bool = False, out: torch.Tensor = None,
+                    work: torch.Tensor = None) -> torch.Tensor:
+    """The Gaussian filter layer on the redundancy weight (Sec. 3.1), or its
+    transpose: W is [V, n_mu, n_s] FP32 on the GPU."""
+    if not isinstance(W, torch.Tensor) or W.dim() != 3:
+        raise ValueError("W must be a [V, n_mu, n_s] tensor")
+    _need(W, "W", torch.float32, tuple(W.shape))
+    out = torch.empty_like(W) if out is None else out
+    work = torch.empty_like(W) if work is None else work
+    _need(out, "out", torch.float32, tuple(W.shape))
+    _need(work, "work", torch.float32, tuple(W.shape))
+    V, n_mu, n_s = W.shape
+    check(_lib.load().dc_gauss_smooth(V, n_mu, n_s, float(sigma), int(radius),
+                                      int(bool(adjoint)), _ptr(W), _ptr(out), _ptr(work),
+                                      _stream()), "dc_gauss_smooth")
+    return out
+
+
 def dc_sync_status(geom: Geometry):
     """Wait for the current stream; raise if a device-side wait timed out."""
     check(_lib.load().dc_sync_status(geom.handle, _stream()), "dc_sync_status")

@@ -60,23 +60,55 @@ def reconstruct(g: torch.Tensor, W: Optional[torch.Tensor], geom: api.Geometry,
     return DefriseClackFunction.apply(g, W, geom, relu, view_chunk)
 
 
+class GaussSmoothFunction(torch.autograd.Function):
+    """The Gaussian filter layer on W (Sec. 3.1); backward is its transpose."""
+
+    @staticmethod
+    def forward(ctx, W: torch.Tensor, sigma: float, radius: int):
+        ctx.sigma, ctx.radius = sigma, radius
+        return api.dc_gauss_smooth(W.contiguous(), sigma, radius)
+
+    @staticmethod
+    def backward(ctx, grad: torch.Tensor):
+        gW = api.dc_gauss_smooth(grad.contiguous(), ctx.sigma, ctx.radius, adjoint=True)
+        return gW, None, None
+
+
+def gauss_smooth(W: torch.Tensor, sigma: float = 20.0, radius: int = 60) -> torch.Tensor:
+    """Differentiable Gaussian filter layer on the redundancy weight."""
+    return GaussSmoothFunction.apply(W, sigma, radius)
+
+
 class DefriseClackNet(torch.nn.Module):
     """The reconstruction network with a learnable redundancy weight W.
 
     W has shape [V, n_mu, n_s] (entry k on the half grid s_{k+1/2}) and is
     multiplied by K = -(1/4pi^2)|v.theta|/sqrt(s^2+D^2) inside the library,
-    so W = 1/2 is the exact full-circle value (Eq. 14).
+    so W = 1/2 is the exact full-circle value (Eq. 14).  With `smooth` =
+    (sigma, radius) the Gaussian filter layer of Sec. 3.1 (sigma 20, kernel
+    121: (20.0, 60)) acts on W before the filter.  `init` is a constant or
+    "uniform" (U[0, 1]: the paper's U[-1, 0] initialisation of its w_red,
+    whose sign K carries here).
     """
 
-    def __init__(self, geom: api.Geometry, init: float = 0.5, relu: bool = True,
-                 view_chunk: int = 0, device=None):
+    def __init__(self, geom: api.Geometry, init=0.5, relu: bool = True,
+                 view_chunk: int = 0, device=None, smooth=None, seed: int = 0):
         super().__init__()
         self.geom = geom
         self.relu = relu
         self.view_chunk = view_chunk
+        self.smooth = smooth
         shape = (geom.V,) + geom.sino_shape
-        self.W = torch.nn.Parameter(torch.full(shape, float(init), device=device,
-                                               dtype=torch.float32))
+        if init == "uniform":
+            gen = torch.Generator(device="cpu").manual_seed(seed)
+            W0 = torch.rand(shape, generator=gen, dtype=torch.float32).to(device)
+        else:
+            W0 = torch.full(shape, float(init), device=device, dtype=torch.float32)
+        self.W = torch.nn.Parameter(W0)
+
+    def weights(self) -> torch.Tensor:
+        """The redundancy weight the filter uses (after smoothing, if any)."""
+        return gauss_smooth(self.W, *self.smooth) if self.smooth else self.W
 
     def forward(self, g: torch.Tensor) -> torch.Tensor:
-        return reconstruct(g, self.W, self.geom, self.relu, self.view_chunk)
+        return reconstruct(g, self.weights(), self.geom, self.relu, self.view_chunk)

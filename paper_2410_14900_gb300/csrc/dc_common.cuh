@@ -44,6 +44,7 @@ enum KernelId {
   KID_SINO_IN,
   KID_BP3D,
   KID_BP3D_ADJ,
+  KID_SMOOTH,
   KID_COUNT
 };
 
