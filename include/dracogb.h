@@ -188,6 +188,27 @@ int dc_backproject_adjoint(const dc_geometry *geom, int B, const float *grad_vol
                            const float *relu_vol, float *grad_gF, void *stream);
 
 /*
+ * dc_reconstruct_host -- Eq. 12 from host projections to a host volume
+ * (dc_filter followed by dc_backproject) with the transfers overlapped:
+ * the projections go up in view chunks on an internal copy stream, each
+ * chunk's filter waiting only for its own upload, and the volume is
+ * backprojected in n_slabs z-slabs (0: 4) whose downloads overlap the later
+ * slabs.  The result equals dc_filter + dc_backproject on the same data.
+ *   g_host  : host, [B][V][H][W] FP32; vol_host: host, [B][Z][Y][X] FP32.
+ *             Page-locked memory (cudaHostAlloc / pinned tensors) is needed
+ *             for the overlap; pageable memory works but serialises.
+ *   g_dev, gF, vol_dev: device buffers of the sizes dc_filter and
+ *             dc_backproject take (caller-owned; g_dev receives the upload).
+ *   W, dtype, gF_scale, flags: as for dc_filter / dc_backproject.
+ * All work is ordered on `stream`: when it completes, vol_host holds the
+ * volume.  The first call on a handle creates its two internal streams and
+ * events (released by dc_destroy_geometry).
+ */
+int dc_reconstruct_host(const dc_geometry *geom, int B, const float *g_host, const float *W,
+                        float *g_dev, void *gF, int dtype, float *gF_scale, float *vol_dev,
+                        float *vol_host, unsigned flags, int n_slabs, void *stream);
+
+/*
  * dc_crofton_weights -- the smooth Crofton weights of Eq. 9 as redundancy
  * weights W for dc_filter (the analytic alternative to learned weights):
  *   M(theta, lambda_i) = |v_i.theta|^m c_i / sum_alpha |v_alpha.theta|^m c_alpha

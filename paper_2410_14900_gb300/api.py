@@ -352,3 +352,39 @@ def reconstruct(geom: Geometry, g: torch.Tensor, W: Optional[torch.Tensor] = Non
     """Eq. 12: f = A3d^T w_d A2d^T D w_red w_sino D A2d w_cos g."""
     gF, sc = dc_filter(geom, g, W, dtype)
     return dc_backproject(geom, gF, sc, kahan=kahan, relu=relu)
+
+
+def dc_reconstruct_host(geom: Geometry, g_host: torch.Tensor, vol_host: torch.Tensor,
+                        W: Optional[torch.Tensor] = None, dtype: str = "f32",
+                        kahan: bool = False, relu: bool = False, n_slabs: int = 0,
+                        g_dev: Optional[torch.Tensor] = None, gF: Optional[torch.Tensor] = None,
+                        scale: Optional[torch.Tensor] = None,
+                        vol_dev: Optional[torch.Tensor] = None, device="cuda") -> torch.Tensor:
+    """Eq. 12 from host projections [B, V, H, W] into the host volume
+    [B, Z, Y, X], the transfers overlapped with the kernels (pin both host
+    tensors for the overlap).  Device buffers are made when not given."""
+    if g_host.is_cuda or vol_host.is_cuda:
+        raise ValueError("g_host and vol_host must be host tensors")
+    B = g_host.shape[0]
+    shp = (B, geom.V, geom.H, geom.W)
+    for t, name, s in ((g_host, "g_host", shp), (vol_host, "vol_host", (B,) + geom.vol_shape)):
+        if t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != s:
+            raise ValueError(f"{name} must be contiguous float32 of shape {s}")
+    code, tdt = _DTYPES[dtype]
+    if W is not None:
+        _need(W, "W", torch.float32, (geom.V,) + geom.sino_shape)
+    g_dev = torch.empty(shp, device=device, dtype=torch.float32) if g_dev is None else g_dev
+    gF = torch.empty(shp, device=device, dtype=tdt) if gF is None else gF
+    vol_dev = torch.empty((B,) + geom.vol_shape, device=device) if vol_dev is None else vol_dev
+    if code == DC_F16 and scale is None:
+        scale = torch.empty((B, geom.V), device=device, dtype=torch.float32)
+    _need(g_dev, "g_dev", torch.float32, shp)
+    _need(gF, "gF", tdt, shp)
+    _need(vol_dev, "vol_dev", torch.float32, (B,) + geom.vol_shape)
+    flags = (DC_KAHAN if kahan else 0) | (DC_RELU if relu else 0)
+    check(_lib.load().dc_reconstruct_host(geom.handle, B, g_host.data_ptr(), _ptr(W), _ptr(g_dev),
+                                          _ptr(gF), code,
+                                          _ptr(scale if code == DC_F16 else None), _ptr(vol_dev),
+                                          vol_host.data_ptr(), flags, int(n_slabs), _stream()),
+          "dc_reconstruct_host")
+    return vol_host

@@ -37,6 +37,7 @@ struct BPArgs {
   unsigned flags;
   int V, H, W, nx, ny, nz, B;
   float dx, dy, dz;
+  int z_begin, z_end;  // voxel planes [z_begin, z_end) of the staged kernels
 };
 
 template <typename T>
@@ -291,9 +292,9 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
   const int hw = tid >> 4, l16 = tid & 15;
   const int ix = bxi * TB_TX + ((hw & 3) << 2) + (l16 & 3);
   const int iy = byi * TB_TY + ((hw >> 2) << 2) + (l16 >> 2);
-  const int zblocks = (a.nz + NZ - 1) / NZ;
+  const int zblocks = (a.z_end - a.z_begin + NZ - 1) / NZ;
   const int b = bzi / zblocks;
-  const int z0 = (bzi % zblocks) * NZ;
+  const int z0 = a.z_begin + (bzi % zblocks) * NZ;
   const float cx = 0.5f * (float)(a.nx - 1), cy = 0.5f * (float)(a.ny - 1),
               cz = 0.5f * (float)(a.nz - 1);
   const float xo = ((float)ix - cx) * a.dx;
@@ -305,7 +306,7 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
   const float by0 = ((float)(byi * TB_TY) - cy) * a.dy;
   const float by1 = ((float)min(byi * TB_TY + TB_TY - 1, a.ny - 1) - cy) * a.dy;
   const float bz0 = zo;
-  const float bz1 = ((float)min(z0 + NZ - 1, a.nz - 1) - cz) * a.dz;
+  const float bz1 = ((float)min(z0 + NZ - 1, a.z_end - 1) - cz) * a.dz;
   const size_t np = (size_t)a.H * a.W;
   const T *gbase = (const T *)a.gF + (size_t)b * a.V * np;
 
@@ -587,7 +588,7 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
 #pragma unroll
   for (int k = 0; k < NZ; ++k) {
     int iz = z0 + k;
-    if (iz >= a.nz) break;
+    if (iz >= a.z_end) break;
     size_t o = (size_t)b * nvox + ((size_t)iz * a.ny + iy) * a.nx + ix;
     float f = acc[k];
     if (a.flags & DC_ACCUM) f += vol[o];
@@ -908,7 +909,7 @@ int launch_bp_tma_nz(const dc_geometry *g, BPArgs &a, bool kahan, cudaStream_t s
                      const CUtensorMap &mn, const CUtensorMap &mw) {
   dim3 blk(TB_TX, TB_TY);
   dim3 grid((a.nx + TB_TX - 1) / TB_TX, (a.ny + TB_TY - 1) / TB_TY,
-            ((a.nz + NZ - 1) / NZ) * a.B);
+            ((a.z_end - a.z_begin + NZ - 1) / NZ) * a.B);
   const size_t sm = bp_tma_smem<T>();
   if (kahan) {
     DC_CUDA(cudaFuncSetAttribute(k_bp3d_tma<T, true, NZ>,
@@ -954,7 +955,68 @@ int check_bp(const dc_geometry *g, int B, const char *who) {
   return DC_OK;
 }
 
+BPArgs bp_args(const dc_geometry *g, int B, const void *gF, int dtype, const float *gF_scale,
+               float *vol, unsigned flags) {
+  const dc_geometry_desc &d = g->d;
+  BPArgs a;
+  a.gF = gF;
+  a.scale = (dtype == DC_F16) ? gF_scale : nullptr;
+  a.views = g->bpv;
+  a.vol = vol;
+  a.flags = flags;
+  a.V = d.n_views;
+  a.H = d.det_rows;
+  a.W = d.det_cols;
+  a.nx = d.vol_x;
+  a.ny = d.vol_y;
+  a.nz = d.vol_z;
+  a.z_begin = 0;
+  a.z_end = d.vol_z;
+  a.B = B;
+  a.dx = (float)d.voxel[0];
+  a.dy = (float)d.voxel[1];
+  a.dz = (float)d.voxel[2];
+  return a;
+}
+
 }  // namespace
+
+namespace dc {
+
+int backproject_check(const dc_geometry *g, int B, const void *gF, int dtype,
+                      const float *gF_scale, const float *vol, unsigned flags, const char *who) {
+  int rc = check_bp(g, B, who);
+  if (rc) return rc;
+  if (!gF || !vol) return fail(DC_ERR_ARG, std::string(who) + ": NULL gF or vol");
+  if (flags & ~(DC_ACCUM | DC_KAHAN | DC_RELU))
+    return fail(DC_ERR_ARG, std::string(who) + ": unknown flag");
+  if (dtype != DC_F32 && dtype != DC_BF16 && dtype != DC_F16)
+    return fail(DC_ERR_ARG, std::string(who) + ": unknown dtype");
+  if (dtype == DC_F16 && !gF_scale)
+    return fail(DC_ERR_ARG, std::string(who) + ": DC_F16 needs gF_scale");
+  return DC_OK;
+}
+
+int backproject_slab(const dc_geometry *g, int B, const void *gF, int dtype,
+                     const float *gF_scale, float *vol, unsigned flags, int z_begin, int z_end,
+                     cudaStream_t st, bool *used) {
+  BPArgs a = bp_args(g, B, gF, dtype, gF_scale, vol, flags);
+  a.z_begin = z_begin;
+  a.z_end = z_end;
+  const bool kahan = (flags & DC_KAHAN) != 0;
+  ProfScope ps(KID_BP3D, st);
+  int rc;
+  switch (dtype) {
+    case DC_F32: rc = launch_bp_tma<float>(g, a, dtype, kahan, st, used); break;
+    case DC_BF16: rc = launch_bp_tma<__nv_bfloat16>(g, a, dtype, kahan, st, used); break;
+    default: rc = launch_bp_tma<__half>(g, a, dtype, kahan, st, used); break;
+  }
+  if (rc) return rc;
+  if (*used) DC_CHECK_LAUNCH("k_bp3d_tma");
+  return DC_OK;
+}
+
+}  // namespace dc
 
 extern "C" {
 
@@ -980,6 +1042,8 @@ int dc_backproject(const dc_geometry *g, int B, const void *gF, int dtype,
   a.nx = d.vol_x;
   a.ny = d.vol_y;
   a.nz = d.vol_z;
+  a.z_begin = 0;
+  a.z_end = d.vol_z;
   a.B = B;
   a.dx = (float)d.voxel[0];
   a.dy = (float)d.voxel[1];
@@ -1120,6 +1184,8 @@ int build_batch_tables(dc_batch *b) {
     P.a.nx = d.vol_x;
     P.a.ny = d.vol_y;
     P.a.nz = d.vol_z;
+    P.a.z_begin = 0;
+    P.a.z_end = d.vol_z;
     P.a.B = 1;
     P.a.dx = (float)d.voxel[0];
     P.a.dy = (float)d.voxel[1];

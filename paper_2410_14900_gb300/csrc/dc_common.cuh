@@ -151,6 +151,10 @@ struct dc_geometry {
   float *w_sinoB;            // [chunk][n_mu][NSp]
   unsigned *w_absmax;        // [chunk]
   unsigned *w_flags;         // [4] device-side error bits (bit 0: wait timeout)
+  // streams and events of dc_reconstruct_host (created by its first call)
+  int aux_ready;
+  cudaStream_t aux_copy, aux_compute;
+  cudaEvent_t aux_ev[8];
 };
 
 namespace dc {
@@ -158,6 +162,22 @@ namespace dc {
 // host-side helpers defined in dc_filter.cu / dc_backproject.cu
 int alloc_workspace(dc_geometry *g);
 int build_mu_tables(dc_geometry *g);
+// argument checks of the filter entry points (DC_OK or the error code)
+int filter_check(const dc_geometry *g, int B, const float *gin, const void *gF, int dtype,
+                 const float *gF_scale, const char *who);
+// chunk sizes: bc batch items of cv views per chunk of the work area
+void filter_chunk_plan(const dc_geometry *g, int B, int *bc, int *cv);
+// the filter of one chunk: views [v0, v0 + nv) of items [b0, b0 + bc)
+int filter_chunk(const dc_geometry *g, const float *gin, const float *W, void *gF, int dtype,
+                 float *gF_scale, int b0, int bc, int v0, int nv, cudaStream_t st);
+// checks of dc_backproject's arguments
+int backproject_check(const dc_geometry *g, int B, const void *gF, int dtype,
+                      const float *gF_scale, const float *vol, unsigned flags, const char *who);
+// backprojection of the z range [z_begin, z_end) of every batch item with the
+// TMA kernel; *used = false (nothing launched) when that kernel cannot run
+int backproject_slab(const dc_geometry *g, int B, const void *gF, int dtype,
+                     const float *gF_scale, float *vol, unsigned flags, int z_begin, int z_end,
+                     cudaStream_t st, bool *used);
 // FP64 split of v into hi (12 fractional bits) + lo
 inline __host__ __device__ float split_hi12(double v) {
   return (float)(rint(v * 4096.0) / 4096.0);

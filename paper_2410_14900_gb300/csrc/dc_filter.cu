@@ -851,6 +851,58 @@ int alloc_workspace(dc_geometry *g) {
   return DC_OK;
 }
 
+int filter_check(const dc_geometry *g, int B, const float *gin, const void *gF, int dtype,
+                 const float *gF_scale, const char *who) {
+  int rc = check_common(g, B, who);
+  if (rc) return rc;
+  if (!gin || !gF) return fail(DC_ERR_ARG, std::string(who) + ": NULL g or gF");
+  if (dtype != DC_F32 && dtype != DC_BF16 && dtype != DC_F16)
+    return fail(DC_ERR_ARG, std::string(who) + ": unknown dtype");
+  if (dtype == DC_F16 && !gF_scale)
+    return fail(DC_ERR_ARG, std::string(who) + ": DC_F16 needs gF_scale");
+  const dc_geometry_desc &d = g->d;
+  if (d.ds < d.pitch * (1.0 - 1e-12))
+    return fail(DC_ERR_UNSUPPORTED, std::string(who) + ": ds < pitch is not supported");
+  return DC_OK;
+}
+
+void filter_chunk_plan(const dc_geometry *g, int B, int *bc, int *cv) {
+  Chunking ck = chunking(g, B);
+  *bc = ck.bc;
+  *cv = ck.cv;
+}
+
+// the filter of images (view v0 + n / bc, item b0 + n % bc), n < nv * bc
+int filter_chunk(const dc_geometry *g, const float *gin, const float *W, void *gF, int dtype,
+                 float *gF_scale, int b0, int bc, int v0, int nv, cudaStream_t st) {
+  const dc_geometry_desc &d = g->d;
+  const int n_img = nv * bc;
+  int rc;
+  if ((rc = launch_prep(g, gin, WT_COS, v0, n_img, bc, b0, st))) return rc;
+  LineArgs la = line_args(g, bc, v0, b0, n_img);
+  la.Wred = W;
+  la.out = g->w_sinoA;
+  if ((rc = launch_linesum<M_FILTER>(g, la, st))) return rc;
+  BP2Args ba = bp2_args(g, bc, v0, b0, n_img, g->w_sinoA);
+  ba.weight = WT_D;
+  if (dtype == DC_F16) {
+    DC_CUDA(cudaMemsetAsync(g->w_absmax, 0, sizeof(unsigned) * n_img, st));
+    ba.out_kind = OUT_F32_ABSMAX;
+    ba.out = g->w_img;
+    if ((rc = launch_bp2d(g, ba, st))) return rc;
+    dim3 grid(64, n_img);
+    ProfScope ps(KID_TO_F16, st);
+    k_to_f16<<<grid, 256, 0, st>>>(g->w_img, g->w_absmax, d.det_rows, d.det_cols, g->Wp,
+                                   d.n_views, bc, v0, b0, (__half *)gF, gF_scale);
+    DC_CHECK_LAUNCH("k_to_f16");
+  } else {
+    ba.out_kind = (dtype == DC_BF16) ? OUT_BF16 : OUT_F32;
+    ba.out = gF;
+    if ((rc = launch_bp2d(g, ba, st))) return rc;
+  }
+  return DC_OK;
+}
+
 }  // namespace dc
 
 extern "C" {
@@ -861,45 +913,16 @@ extern "C" {
 
 int dc_filter(const dc_geometry *g, int B, const float *gin, const float *W, void *gF,
               int dtype, float *gF_scale, void *stream) {
-  int rc = check_common(g, B, "dc_filter");
+  int rc = dc::filter_check(g, B, gin, gF, dtype, gF_scale, "dc_filter");
   if (rc) return rc;
-  if (!gin || !gF) return dc::fail(DC_ERR_ARG, "dc_filter: NULL g or gF");
-  if (dtype != DC_F32 && dtype != DC_BF16 && dtype != DC_F16)
-    return dc::fail(DC_ERR_ARG, "dc_filter: unknown dtype");
-  if (dtype == DC_F16 && !gF_scale)
-    return dc::fail(DC_ERR_ARG, "dc_filter: DC_F16 needs gF_scale");
-  const dc_geometry_desc &d = g->d;
-  if (d.ds < d.pitch * (1.0 - 1e-12))
-    return dc::fail(DC_ERR_UNSUPPORTED, "dc_filter: ds < pitch is not supported");
   cudaStream_t st = (cudaStream_t)stream;
-  Chunking ck = chunking(g, B);
-  for (int b0 = 0; b0 < B; b0 += ck.bc) {
-    int bc = std::min(ck.bc, B - b0);
-    for (int v0 = 0; v0 < d.n_views; v0 += ck.cv) {
-      int nv = std::min(ck.cv, d.n_views - v0);
-      int n_img = nv * bc;
-      if ((rc = launch_prep(g, gin, WT_COS, v0, n_img, bc, b0, st))) return rc;
-      LineArgs la = line_args(g, bc, v0, b0, n_img);
-      la.Wred = W;
-      la.out = g->w_sinoA;
-      if ((rc = launch_linesum<M_FILTER>(g, la, st))) return rc;
-      BP2Args ba = bp2_args(g, bc, v0, b0, n_img, g->w_sinoA);
-      ba.weight = WT_D;
-      if (dtype == DC_F16) {
-        DC_CUDA(cudaMemsetAsync(g->w_absmax, 0, sizeof(unsigned) * n_img, st));
-        ba.out_kind = OUT_F32_ABSMAX;
-        ba.out = g->w_img;
-        if ((rc = launch_bp2d(g, ba, st))) return rc;
-        dim3 grid(64, n_img);
-        dc::ProfScope ps(dc::KID_TO_F16, st);
-        k_to_f16<<<grid, 256, 0, st>>>(g->w_img, g->w_absmax, d.det_rows, d.det_cols, g->Wp,
-                                       d.n_views, bc, v0, b0, (__half *)gF, gF_scale);
-        DC_CHECK_LAUNCH("k_to_f16");
-      } else {
-        ba.out_kind = (dtype == DC_BF16) ? OUT_BF16 : OUT_F32;
-        ba.out = gF;
-        if ((rc = launch_bp2d(g, ba, st))) return rc;
-      }
+  int bcm, cvm;
+  dc::filter_chunk_plan(g, B, &bcm, &cvm);
+  for (int b0 = 0; b0 < B; b0 += bcm) {
+    int bc = std::min(bcm, B - b0);
+    for (int v0 = 0; v0 < g->d.n_views; v0 += cvm) {
+      int nv = std::min(cvm, g->d.n_views - v0);
+      if ((rc = dc::filter_chunk(g, gin, W, gF, dtype, gF_scale, b0, bc, v0, nv, st))) return rc;
     }
   }
   return DC_OK;

@@ -165,6 +165,11 @@ void free_geometry(dc_geometry *g) {
   cudaFree(g->w_sinoB);
   cudaFree(g->w_absmax);
   cudaFree(g->w_flags);
+  if (g->aux_ready) {
+    cudaStreamDestroy(g->aux_copy);
+    cudaStreamDestroy(g->aux_compute);
+    for (int i = 0; i < 8; ++i) cudaEventDestroy(g->aux_ev[i]);
+  }
   free(g->host_geo);
   delete g;
 }
