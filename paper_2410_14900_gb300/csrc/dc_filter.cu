@@ -7,12 +7,14 @@
 // and its reverse mode.  Views are processed in chunks of images (view x
 // batch item) so that the work area stays in L2:
 //
-//   k_prep      weight (w_cos or w_d) and write the image and its transpose
+//   k_prep      weight (w_cos or w_d) and write the image with padded rows
 //   k_linesum   Joseph line sums of every (mu, s) line of an image, streamed
-//               row band by row band through shared memory with bulk copies;
-//               neighbouring lines of a warp take the s-difference by shuffle
-//               so that D_f never subtracts two large sums; the epilogue
-//               applies w_sino, K, W and D_b (or the adjoint chain)
+//               band by band (32, 16 or 8 detector rows or columns) through
+//               shared memory by asynchronous copies, each band stored with
+//               the band step as the fastest index; neighbouring lines of a
+//               warp take the s-difference by shuffle so that D_f never
+//               subtracts two large sums; the epilogue applies w_sino, K, W
+//               and D_b (or the adjoint chain)
 //   k_bp2d      pixel-driven A2d^T: each pixel gathers the two sinogram taps
 //               of every angle (the exact transpose of the Joseph weights),
 //               angles streamed through shared memory with bulk copies; the
