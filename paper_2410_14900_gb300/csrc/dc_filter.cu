@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_prep(PrepArgs a) {
 // ------------------------------------------------------------- line sums
 enum { M_RAW = 0, M_GRANGEAT = 1, M_FILTER = 2, M_DIFFSTORE = 3, M_ADJ = 4 };
 
-constexpr int LS_THREADS = 512;  // one CTA per SM
+constexpr int LS_THREADS = 640;  // one CTA per SM: 20 warps at 96 registers
 constexpr int LS_WARPS = LS_THREADS / 32;
 // A band of RB detector rows (32, or 16 / 8 when long detector rows would
 // not fit) is staged with RB + 1 floats per sample: odd, so lanes at distinct
@@ -87,7 +87,7 @@ constexpr int LS_WARPS = LS_THREADS / 32;
 // meets the detector anywhere in a band moves less than RB samples (slope at
 // most 1) over the band, so its taps never leave the stage and need no clamp.
 constexpr int LS_SMEM_BUDGET = 225 * 1024;  // one CTA per SM
-static_assert(LS_WARPS * 16 == dc::DC_LS_MAX_TASKS, "task table size");
+static_assert(LS_WARPS <= dc::DC_LS_MAX_TASKS, "task table size");
 
 struct LineArgs {
   const float *img;   // [n][H][Wp]
