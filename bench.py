@@ -187,6 +187,15 @@ def oracle_sample(w, g_np, n_views_sample: int, n_vox_sample: int, seed: int = 0
     return ms, sample, orc.num_threads(), t_f + t_b
 
 
+def workload_config(w, storage: str, B: int, world: int) -> dict:
+    """The `config` both arms report for a workload."""
+    return {"workload": w.name, "orbit": w.orbit.kind, "views": w.n_views,
+            "detector": [w.det_rows, w.det_cols], "pitch_mm": w.pitch,
+            "planes": [w.n_mu, w.n_s], "volume": list(w.vol_shape),
+            "voxel_mm": list(w.voxel), "storage": storage,
+            "batch_per_gpu": B, "parallelism": f"replicas x{world}"}
+
+
 # --------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     """The oracle (this tier's reference) on the host cores, rank 0 only."""
@@ -212,7 +221,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": val,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name},
+            "data": "synthetic", "config": workload_config(w, args.storage, 1, world),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -576,13 +585,9 @@ def run_ours(args, rank, world, local_rank):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic: seeded 20-ellipsoid phantom, exact line integrals",
-                "config": {"workload": w.name, "orbit": w.orbit.kind, "views": V,
-                           "detector": [H, Wd], "pitch_mm": w.pitch,
-                           "planes": [w.n_mu, w.n_s], "volume": list(w.vol_shape),
-                           "voxel_mm": list(w.voxel), "storage": args.storage,
-                           "batch_per_gpu": B, "parallelism": f"replicas x{world}",
-                           "tuning": {k: tuned[k] for k in ("chunk_images", "bp_nz")},
-                           "l2": "inputs larger than L2 (g 390 MB, f 537 MB), no flush"},
+                "config": dict(workload_config(w, args.storage, B, world),
+                               tuning={k: tuned[k] for k in ("chunk_images", "bp_nz")},
+                               l2="inputs larger than L2 (g 390 MB, f 537 MB), no flush"),
                 "roofline": roof, "breakdown": breakdown, "forms": forms, "train_step": train,
                 "batched": batched, "paper_shape": paper_shape,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(n_launch),
