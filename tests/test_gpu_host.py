@@ -67,3 +67,26 @@ def test_host_pipeline_back_to_back_calls_reuse_buffers():
         ref = api.reconstruct(geom, torch.as_tensor(g, device="cuda"))
         torch.cuda.synchronize()
         assert rel_l2(vh.double().numpy(), ref.double().cpu().numpy()) < 1e-6
+
+
+def test_host_pipeline_argument_errors():
+    from paper_2410_14900_gb300 import _lib as L
+    case = circle64()
+    geom = api.Geometry(case.desc, case.P, case.vdl)
+    Lh = L.load()
+    shp = (1, geom.V, geom.H, geom.W)
+    gd = torch.empty(shp, device="cuda")
+    gF = torch.empty(shp, device="cuda")
+    vd = torch.empty((1,) + geom.vol_shape, device="cuda")
+    gh = torch.empty(shp).pin_memory()
+    vh = torch.empty((1,) + geom.vol_shape).pin_memory()
+    args = [geom.handle, 1, gh.data_ptr(), None, gd.data_ptr(), gF.data_ptr(), L.DC_F32, None,
+            vd.data_ptr(), vh.data_ptr(), 0, 0, None]
+    for i, bad in ((2, None), (9, None), (4, None), (8, None), (11, -1), (1, 0), (10, 64),
+                   (6, 7)):
+        a = list(args)
+        a[i] = bad
+        assert Lh.dc_reconstruct_host(*a) == L.DC_ERR_ARG, (i, bad)
+    assert Lh.dc_reconstruct_host(*args) == L.DC_OK
+    torch.cuda.synchronize()
+    api.dc_sync_status(geom)
