@@ -81,7 +81,7 @@ typedef struct {
   int n_mu;             /* angles of the per-view 2D Radon transform      */
   int n_s;              /* s-bins of the per-view 2D Radon transform      */
   double pitch;         /* detector pixel pitch (mm), square pixels       */
-  double ds;            /* s-bin spacing (mm), ds >= pitch                */
+  double ds;            /* s-bin spacing (mm), ds >= pitch / 3            */
   int vol_x, vol_y, vol_z;
   double voxel[3];      /* voxel size (dx, dy, dz) in mm                  */
   double vol_center[3]; /* world position of the volume centre (mm)       */
@@ -138,7 +138,7 @@ int dc_get_view_geometry(const dc_geometry *geom, double *out);
  *             DC_F16).
  *   gF_scale: device, [B][V] FP32, required for DC_F16 (g^F = half * scale),
  *             ignored otherwise.
- * Requires ds >= pitch.
+ * Requires ds >= pitch / 3 (below pitch a pixel meets up to six lines).
  */
 int dc_filter(const dc_geometry *geom, int B, const float *g, const float *W, void *gF,
               int dtype, float *gF_scale, void *stream);

@@ -417,7 +417,8 @@ struct BPMu {
   float w1c, lo, hi;        // 1 - winv; positions relative to I00 clamp to [lo, hi]
   unsigned cbase;           // byte offset of s-bin I00 in its stage, minus the floor's exponent bits
   int fast;                 // positions stay inside (lo, hi) over the tile: no clamp
-  int pad0, pad1, pad2;
+  int row0;                 // float offset of s-bin I00 in its stage
+  int pad1, pad2;
 };
 
 // the two sinogram taps around s-bin position x (relative to a row anchor
@@ -431,6 +432,10 @@ __device__ __forceinline__ float taps(const char *sb, unsigned cb, float x, floa
   return x - (t - M);
 }
 
+// MULTI: ds < pitch, where the transposed Joseph hat of an angle (half-width
+// 1/winv s-bins, at most 3 for ds >= pitch/3) covers up to six taps; those
+// are summed with explicit bounds instead of the two-tap fast paths.
+template <bool MULTI>
 __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
   extern __shared__ __align__(16) float smem[];
   __shared__ uint64_t bars[2];
@@ -492,7 +497,8 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
       float xmin = M.F00 + fminf(ex, 0.0f) + fminf(ey, 0.0f);
       float xmax = M.F00 + fmaxf(ex, 0.0f) + fmaxf(ey, 0.0f);
       M.fast = (xmin >= M.lo + 0.01f && xmax <= M.hi - 0.01f) ? 1 : 0;
-      M.pad0 = M.pad1 = M.pad2 = 0;
+      M.row0 = mi * rstride + PADL + (int)I00;
+      M.pad1 = M.pad2 = 0;
       bmu[c & 1][mi] = M;
     }
   };
@@ -528,7 +534,29 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
     for (int mi = 0; mi < nm; ++mi) {
       const BPMu M = bmu[c & 1][mi];
       const unsigned cb = M.cbase + st_off;
-      if (M.fast) {
+      if (MULTI) {
+        // taps k = floor(x) - 2 .. floor(x) + 3 (relative to I00) inside the
+        // s range [lo + 1, hi - 1]; weight max(0, 1 - winv |x - k|)
+        const float *row = smem + (c & 1) * stage_sz + M.row0;
+        const int klo = (int)M.lo + 1, khi = (int)M.hi - 1;
+#pragma unroll
+        for (int ry = 0; ry < BP2_RY; ++ry) {
+          float rt = fmaf(rlf[ry], M.Bs, M.F00);
+#pragma unroll
+          for (int q = 0; q < BP2_NQ; ++q) {
+            float f;
+            const int k0 = dc::floor_frac(fmaf(jlf[q], M.Bc, rt), f);
+            float sum = 0.0f;
+#pragma unroll
+            for (int t = -2; t <= 3; ++t) {
+              const int kk = k0 + t;
+              const float w = fmaxf(0.0f, fmaf(-fabsf(f - (float)t), M.winv, 1.0f));
+              if (kk >= klo && kk <= khi) sum = fmaf(w, row[kk], sum);
+            }
+            acc[ry][q] += sum;
+          }
+        }
+      } else if (M.fast) {
 #pragma unroll
         for (int ry = 0; ry < BP2_RY; ++ry) {
           float rt = fmaf(rlf[ry], M.Bs, M.F00);
@@ -703,17 +731,24 @@ int launch_linesum(const dc_geometry *g, LineArgs &a, cudaStream_t st) {
   }
 }
 
+bool multi_tap(const dc_geometry *g) { return g->d.ds < g->d.pitch * (1.0 - 1e-12); }
+
 int launch_bp2d(const dc_geometry *g, BP2Args &a, cudaStream_t st) {
   size_t sm = bp2d_smem(g);
   static bool attr_done = false;
   if (!attr_done) {
-    DC_CUDA(cudaFuncSetAttribute(k_bp2d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    DC_CUDA(cudaFuncSetAttribute(k_bp2d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    DC_CUDA(cudaFuncSetAttribute(k_bp2d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024));
     attr_done = true;
   }
   dim3 grid((a.W + BP2_TX - 1) / BP2_TX, (a.H + BP2_TY - 1) / BP2_TY, a.n_img);
   dc::ProfScope ps(dc::KID_BP2D, st);
-  k_bp2d<<<grid, BP2_THREADS, sm, st>>>(a);
+  if (multi_tap(g))
+    k_bp2d<true><<<grid, BP2_THREADS, sm, st>>>(a);
+  else
+    k_bp2d<false><<<grid, BP2_THREADS, sm, st>>>(a);
   DC_CHECK_LAUNCH("k_bp2d");
   return DC_OK;
 }
@@ -863,8 +898,8 @@ int filter_check(const dc_geometry *g, int B, const float *gin, const void *gF, 
   if (dtype == DC_F16 && !gF_scale)
     return fail(DC_ERR_ARG, std::string(who) + ": DC_F16 needs gF_scale");
   const dc_geometry_desc &d = g->d;
-  if (d.ds < d.pitch * (1.0 - 1e-12))
-    return fail(DC_ERR_UNSUPPORTED, std::string(who) + ": ds < pitch is not supported");
+  if (3.0 * d.ds < d.pitch * (1.0 - 1e-12))
+    return fail(DC_ERR_UNSUPPORTED, std::string(who) + ": ds < pitch/3 is not supported");
   return DC_OK;
 }
 
@@ -938,8 +973,8 @@ int dc_filter_adjoint(const dc_geometry *g, int B, const float *grad_gF, const f
   if (!grad_gF || !gin) return dc::fail(DC_ERR_ARG, "dc_filter_adjoint: NULL grad_gF or g");
   if (view_chunk < 0) return dc::fail(DC_ERR_ARG, "dc_filter_adjoint: negative view_chunk");
   const dc_geometry_desc &d = g->d;
-  if (d.ds < d.pitch * (1.0 - 1e-12))
-    return dc::fail(DC_ERR_UNSUPPORTED, "dc_filter_adjoint: ds < pitch is not supported");
+  if (3.0 * d.ds < d.pitch * (1.0 - 1e-12))
+    return dc::fail(DC_ERR_UNSUPPORTED, "dc_filter_adjoint: ds < pitch/3 is not supported");
   if (!grad_g && !grad_W) return DC_OK;
   cudaStream_t st = (cudaStream_t)stream;
   Chunking ck = chunking(g, B, view_chunk);
@@ -1023,8 +1058,8 @@ int dc_radon2d_adjoint(const dc_geometry *g, int B, const float *R, float *img, 
   if (rc) return rc;
   if (!img || !R) return dc::fail(DC_ERR_ARG, "dc_radon2d_adjoint: NULL argument");
   const dc_geometry_desc &d = g->d;
-  if (d.ds < d.pitch * (1.0 - 1e-12))
-    return dc::fail(DC_ERR_UNSUPPORTED, "dc_radon2d_adjoint: ds < pitch is not supported");
+  if (3.0 * d.ds < d.pitch * (1.0 - 1e-12))
+    return dc::fail(DC_ERR_UNSUPPORTED, "dc_radon2d_adjoint: ds < pitch/3 is not supported");
   cudaStream_t st = (cudaStream_t)stream;
   Chunking ck = chunking(g, B);
   for (int b0 = 0; b0 < B; b0 += ck.bc) {

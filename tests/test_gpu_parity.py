@@ -185,7 +185,7 @@ def test_argument_errors_on_gpu():
     assert Lh.dc_filter(gg.handle, 1, p, None, p, 7, None, None) == L.DC_ERR_ARG
     assert Lh.dc_filter(gg.handle, 1, p, None, p, L.DC_F16, None, None) == L.DC_ERR_ARG
     assert Lh.dc_backproject(gg.handle, 1, p, 0, None, p, 64, None) == L.DC_ERR_ARG
-    bad = dict(case.desc, ds=case.desc["pitch"] * 0.5)
+    bad = dict(case.desc, ds=case.desc["pitch"] * 0.3)
     g2 = api.Geometry(bad, case.P, case.vdl)
     assert Lh.dc_filter(g2.handle, 1, p, None, p, 0, None, None) == L.DC_ERR_UNSUPPORTED
     with pytest.raises(L.DCError):
@@ -209,3 +209,31 @@ def test_allocation_failure_is_reported():
         break
     else:
         pytest.fail("setup never succeeded")
+
+
+@pytest.mark.parametrize("frac", [0.5, 0.8])
+def test_fine_s_grid_matches_oracle(frac):
+    """ds below the pitch: a pixel meets up to six lines of an angle (the
+    multi-tap 2-D backprojection); filter, its adjoint and A2d^T."""
+    base = ragged(B=1)
+    desc = dict(base.desc, ds=base.desc["pitch"] * frac, n_s=int(base.desc["n_s"] / frac) + 1)
+    gg = api.Geometry(desc, base.P, base.vdl)
+    og = orc.Geometry(desc, base.P, base.vdl)
+    g = phantom_projections(base).astype(np.float32)
+    rng = np.random.default_rng(31)
+    W = rng.uniform(0.2, 0.8, size=(desc["n_views"], desc["n_mu"], desc["n_s"])).astype(np.float32)
+    gF, _ = api.dc_filter(gg, _dev(g), _dev(W))
+    assert rel_l2(_host(gF), orc.filter(og, g, W)) < 1e-4
+    R = rng.normal(size=(1, desc["n_views"], desc["n_mu"], desc["n_s"])).astype(np.float32)
+    img = _host(api.dc_radon2d_adjoint(gg, _dev(R)))
+    for i in range(0, desc["n_views"], 7):
+        cu, cv = og.principal_point(i)
+        ref = orc.radon_T(R[0, i], desc["det_rows"], desc["det_cols"], desc["pitch"], desc["ds"],
+                          cu, cv)
+        assert rel_l2(img[0, i], ref) < 1e-5
+    G = rng.normal(size=g.shape).astype(np.float32)
+    gg_g, gg_W = api.dc_filter_adjoint(gg, _dev(G), _dev(g), _dev(W))
+    rg, rW = orc.filter_adjoint(og, g, G, W)
+    assert rel_l2(_host(gg_g), rg) < 1e-4
+    assert rel_l2(_host(gg_W), rW) < 1e-4
+    api.dc_sync_status(gg)
