@@ -192,8 +192,8 @@ int dc_backproject_adjoint(const dc_geometry *geom, int B, const float *grad_vol
  * (dc_filter followed by dc_backproject) with the transfers overlapped:
  * the projections go up in view chunks on an internal copy stream, each
  * chunk's filter waiting only for its own upload, and the volume is
- * backprojected in n_slabs z-slabs (0: 4) whose downloads overlap the later
- * slabs.  The result equals dc_filter + dc_backproject on the same data.
+ * backprojected in n_slabs z-slabs (0: 16; at most one per 32 or 16 voxel
+ * planes) whose downloads overlap the later slabs.  The result equals dc_filter + dc_backproject on the same data.
  *   g_host  : host, [B][V][H][W] FP32; vol_host: host, [B][Z][Y][X] FP32.
  *             Page-locked memory (cudaHostAlloc / pinned tensors) is needed
  *             for the overlap; pageable memory works but serialises.

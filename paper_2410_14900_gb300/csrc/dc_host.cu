@@ -80,7 +80,7 @@ extern "C" int dc_reconstruct_host(const dc_geometry *geom, int B, const float *
   const size_t nxy = (size_t)d.vol_x * d.vol_y, nvox = nxy * d.vol_z;
   const int zq = g->bp_nz;
   const int zblocks = (d.vol_z + zq - 1) / zq;
-  const int ns = std::max(1, std::min(n_slabs == 0 ? 4 : n_slabs, zblocks));
+  const int ns = std::max(1, std::min(n_slabs == 0 ? 16 : n_slabs, zblocks));
   const int depth = ((zblocks + ns - 1) / ns) * zq;
   int s = 0;
   for (int z0 = 0; z0 < d.vol_z; z0 += depth, ++s) {
