@@ -242,7 +242,7 @@ int dc_crofton_weights(const dc_geometry *geom, int n_seg, const int *seg_start,
  *   adjoint : 0 applies the filter, 1 its transpose.
  * in, out and work must be distinct.  DC_ERR_ARG for bad sizes, sigma <= 0
  * or radius outside [0, 1024]; DC_ERR_UNSUPPORTED when a line and its halo
- * do not fit in shared memory (n_mu or n_s + 3 radius beyond ~25000).
+ * do not fit in shared memory (n_mu or n_s plus 4 radius beyond ~25000).
  */
 int dc_gauss_smooth(int V, int n_mu, int n_s, float sigma, int radius, int adjoint,
                     const float *in, float *out, float *work, void *stream);
