@@ -539,6 +539,9 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_forms and args.storage == "f32":
         forms = {}
         for st in ("bf16", "f16"):
+            # voxels per thread along z tuned for this storage form with Kahan
+            ft = tune.autotune(geom, st, chunks=(tuned["chunk_images"],), nzs=(16, 32), kahan=True)
+            forms[f"{st}_bp_nz"] = ft["bp_nz"]
             gF2 = torch.empty((B, V, H, Wd), device=dev,
                               dtype=torch.bfloat16 if st == "bf16" else torch.float16)
             sc2 = torch.empty((B, V), device=dev) if st == "f16" else None

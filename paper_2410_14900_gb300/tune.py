@@ -61,9 +61,10 @@ def _time(fn, reps=2):
 
 
 def autotune(geom: api.Geometry, dtype: str = "f32", use_cache: bool = True,
-             chunks=(8, 16, 32), nzs=(16, 32)) -> dict:
-    """Pick chunk_images and bp_nz for `geom`, apply them and return them."""
-    key = shape_key(geom, dtype)
+             chunks=(8, 16, 32), nzs=(16, 32), kahan: bool = False) -> dict:
+    """Pick chunk_images and bp_nz for `geom`, apply them and return them
+    (the backprojection timed with Kahan summation when `kahan`)."""
+    key = shape_key(geom, dtype) + ("|kahan" if kahan else "")
     with _lock:
         db = _load() if use_cache else {}
     if key in db:
@@ -85,7 +86,7 @@ def autotune(geom: api.Geometry, dtype: str = "f32", use_cache: bool = True,
     best_c = min(res["filter_ms"], key=res["filter_ms"].get)
     for nz in nzs:
         api.dc_geometry_set_tuning(geom, 0, nz)
-        res["bp_ms"][nz] = _time(lambda: api.dc_backproject(geom, gF, sc, out=vol))
+        res["bp_ms"][nz] = _time(lambda: api.dc_backproject(geom, gF, sc, out=vol, kahan=kahan))
     best_nz = min(res["bp_ms"], key=res["bp_ms"].get)
     api.dc_geometry_set_tuning(geom, best_c, best_nz)
     best = {"chunk_images": int(best_c), "bp_nz": int(best_nz),
