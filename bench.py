@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-paper-shape", action="store_true")
+    ap.add_argument("--no-interp-peak", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched-orbits measurement (for profiling)")
     ap.add_argument("--train-only", action="store_true",
@@ -161,6 +162,31 @@ def work_units(desc, B):
     return {"k_linesum": float(B) * V * rows * n_s,
             "k_bp2d": float(B) * V * n_mu * H * W,
             "k_bp3d": float(B) * V * desc["vol_x"] * desc["vol_y"] * desc["vol_z"]}
+
+
+def interp_peaks(L, dev) -> dict:
+    """Practical peaks of the three gather cores on this GPU (dc_microbench:
+    the bare inner step on a resident shared-memory tile), steps per second."""
+    import torch
+    nb, iters = 152 * 4, 4000
+    sink = torch.empty(nb * 512, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for kind, name in enumerate(("joseph_step", "hat_pair", "bilinear_sample",
+                                 "weighted_sample")):
+        for _ in range(2):
+            L.dc_microbench(kind, nb, 100, sink.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = L.dc_microbench(kind, nb, iters, sink.data_ptr(), stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rc != 0:
+            raise RuntimeError(L.dc_last_error().decode())
+        out[name + "_peak_per_s"] = nb * 512.0 * iters * 32 / (e0.elapsed_time(e1) * 1e-3)
+    return out
 
 
 # --------------------------------------------------------------- CPU oracle
@@ -467,6 +493,7 @@ def run_ours(args, rank, world, local_rank):
             kernels[name] = {"ms_total": float(ms_k[i]), "launches": int(cnt_k[i]),
                              "ms_per_launch": float(ms_k[i] / cnt_k[i])}
     units = work_units(desc, B)
+    interp = interp_peaks(L, dev) if not args.no_interp_peak else None
     peaks, peak_kind = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -488,10 +515,20 @@ def run_ours(args, rank, world, local_rank):
     hbm_bytes = (B * V * H * Wd * 4  # read g
                  + 2 * B * V * H * Wd * gF.element_size()  # write + read g^F
                  + vol.numel() * 4)  # write f
+    if interp:
+        # each kernel's own rate (work units per second of its launches) as
+        # a fraction of the bare inner step's rate on this GPU
+        for kname, kind in (("k_linesum", "joseph_step"), ("k_bp2d", "hat_pair"),
+                            ("k_bp3d", "bilinear_sample"), ("k_bp3d", "weighted_sample")):
+            if kname in kernels:
+                rate = units[kname] * args.steps / (kernels[kname]["ms_total"] * 1e-3)
+                interp[kind + "_kernel_per_s"] = rate
+                interp[kind + "_frac"] = rate / interp[kind + "_peak_per_s"]
     breakdown = {"filter_ms": filter_ms, "backproject_ms": bp_ms,
                  "bp_gups": units["k_bp3d"] / (bp_ms * 1e-3) / 1e9 if bp_ms else None,
                  "algorithmic_hbm_bytes": hbm_bytes,
                  "hbm_frac_of_step": hbm_bytes / (ms_step * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6772.2),
+                 "interp_peak": interp,
                  "kernels": kernels}
 
     # end to end through the public API with host buffers: dc_reconstruct_host

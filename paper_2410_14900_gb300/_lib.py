@@ -56,6 +56,7 @@ _SIGS = {
                                           _P, _P]),
     "dc_reconstruct_host": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, ctypes.c_int, _P, _P,
                                            _P, ctypes.c_uint, ctypes.c_int, _P]),
+    "dc_microbench": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
     "dc_gauss_smooth": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                        ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     "dc_batch_create": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int, ctypes.c_uint,
