@@ -315,7 +315,7 @@ int dc_sync_status(const dc_geometry *geom, void *stream);
 /*
  * dc_radon2d_noalloc -- the Joseph 2D Radon transform of dc_radon2d for
  * callers that cannot allocate device memory: a real-time loop whose memory
- * budget is fixed before the scan and must never wait on the driver's
+ * budget is fixed before the scan and must never wait on CUDA's
  * allocator, or a host that embeds this library inside another runtime's
  * memory pool and cannot create a geometry handle.  The paper has no
  * counterpart; it is an interface variant.  It allocates nothing and needs

@@ -1100,7 +1100,7 @@ int dc_sync_status(const dc_geometry *g, void *stream) {
 //
 // Callers that cannot allocate device memory (a real-time reconstruction
 // loop on a scanner whose memory budget is fixed before the scan and must
-// never wait on the driver's allocator, or a host that embeds this library
+// never wait on CUDA's allocator, or a host that embeds this library
 // inside another runtime's memory pool and cannot create a geometry handle)
 // use dc_radon2d_noalloc.  Its work area is the fixed array below, compiled
 // into the library: every GPU that loads the library holds it until exit.
