@@ -1081,6 +1081,25 @@ int dc_radon2d_adjoint(const dc_geometry *g, int B, const float *R, float *img, 
   return DC_OK;
 }
 
+// Test hook of the timeout path: one thread waits, with the library's bound
+// (~2^31 cycles), on an mbarrier that nothing completes, gives up and raises
+// the handle's timeout flag, as a staged kernel does when a copy never lands.
+__global__ void k_wait_probe(unsigned *err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    dc::mbar_init(&bar, 1);
+    dc::fence_barrier_init();
+    dc::mbar_wait_bounded(&bar, 0, err);
+  }
+}
+
+int dc_debug_wait_timeout(const dc_geometry *g, void *stream) {
+  if (!g) return dc::fail(DC_ERR_ARG, "dc_debug_wait_timeout: NULL geometry");
+  k_wait_probe<<<1, 32, 0, (cudaStream_t)stream>>>(g->w_flags);
+  DC_CHECK_LAUNCH("k_wait_probe");
+  return DC_OK;
+}
+
 int dc_sync_status(const dc_geometry *g, void *stream) {
   if (!g) return dc::fail(DC_ERR_ARG, "dc_sync_status: NULL geometry");
   DC_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
