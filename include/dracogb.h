@@ -313,6 +313,17 @@ int dc_radon2d_adjoint(const dc_geometry *geom, int B, const float *R, float *im
 int dc_sync_status(const dc_geometry *geom, void *stream);
 
 /*
+ * dc_deriv -- the s-derivatives of Eqs. 7 and 11 on their own (the filter
+ * fuses them): in, out device [B][V][n_mu][n_s] FP32, distinct.
+ *   kind 0: D_f, out[k] = (in[k+1] - in[k]) / ds on s_{k+1/2}, out[n_s-1] = 0
+ *   kind 1: D_f^T
+ *   kind 2: D_b, out[k] = (in[k] - in[k-1]) / ds with in[-1] = 0
+ *   kind 3: D_b^T
+ */
+int dc_deriv(const dc_geometry *geom, int B, const float *in, float *out, int kind,
+             void *stream);
+
+/*
  * dc_radon2d_noalloc -- the Joseph 2D Radon transform of dc_radon2d for
  * callers that cannot allocate device memory: a real-time loop whose memory
  * budget is fixed before the scan and must never wait on CUDA's

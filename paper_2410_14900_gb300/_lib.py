@@ -78,6 +78,7 @@ _SIGS = {
     "dc_profile_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "dc_debug_fail_alloc_after": (None, [ctypes.c_long]),
     "dc_debug_wait_timeout": (ctypes.c_int, [_P, _P]),
+    "dc_deriv": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
 }
 
 

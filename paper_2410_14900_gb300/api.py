@@ -269,6 +269,17 @@ def dc_gauss_smooth(W: torch.Tensor, sigma: float = 20.0, radius: int = 60,
     return out
 
 
+def dc_deriv(geom: Geometry, x: torch.Tensor, kind: str = "f") -> torch.Tensor:
+    """The s-derivatives alone on [B, V, n_mu, n_s] sinograms: kind "f"
+    (D_f), "fT", "b" (D_b) or "bT"."""
+    B = x.shape[0]
+    _need(x, "x", torch.float32, (B, geom.V) + geom.sino_shape)
+    out = torch.empty_like(x)
+    code = {"f": 0, "fT": 1, "b": 2, "bT": 3}[kind]
+    check(_lib.load().dc_deriv(geom.handle, B, _ptr(x), _ptr(out), code, _stream()), "dc_deriv")
+    return out
+
+
 def dc_sync_status(geom: Geometry):
     """Wait for the current stream; raise if a device-side wait timed out."""
     check(_lib.load().dc_sync_status(geom.handle, _stream()), "dc_sync_status")

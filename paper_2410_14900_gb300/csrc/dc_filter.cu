@@ -1081,6 +1081,46 @@ int dc_radon2d_adjoint(const dc_geometry *g, int B, const float *R, float *img, 
   return DC_OK;
 }
 
+// The s-derivatives of Eqs. 7 and 11 alone, on [rows][n_s] sinograms:
+// kind 0 D_f (forward difference onto s_{k+1/2}; entry n_s-1 is 0), 1 its
+// transpose, 2 D_b (backward difference, zero below k = 0), 3 its transpose;
+// all divided by ds.  One thread per entry, rows read from global memory.
+__global__ void k_deriv(const float *__restrict__ in, float *__restrict__ out, long long rows,
+                        int n_s, float inv_ds, int kind) {
+  const long long total = rows * n_s;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i % n_s);
+    const float *x = in + (i - k);
+    float v;
+    if (kind == 0) {
+      v = (k < n_s - 1) ? (x[k + 1] - x[k]) * inv_ds : 0.0f;
+    } else if (kind == 1) {
+      const float a = (k >= 1) ? x[k - 1] : 0.0f, b = (k < n_s - 1) ? x[k] : 0.0f;
+      v = (a - b) * inv_ds;
+    } else if (kind == 2) {
+      v = (x[k] - (k > 0 ? x[k - 1] : 0.0f)) * inv_ds;
+    } else {
+      v = (x[k] - (k + 1 < n_s ? x[k + 1] : 0.0f)) * inv_ds;
+    }
+    out[i] = v;
+  }
+}
+
+int dc_deriv(const dc_geometry *g, int B, const float *in, float *out, int kind, void *stream) {
+  int rc = check_common(g, B, "dc_deriv");
+  if (rc) return rc;
+  if (!in || !out || in == out) return dc::fail(DC_ERR_ARG, "dc_deriv: NULL or aliased arrays");
+  if (kind < 0 || kind > 3) return dc::fail(DC_ERR_ARG, "dc_deriv: kind must be 0..3");
+  const dc_geometry_desc &d = g->d;
+  const long long rows = (long long)B * d.n_views * d.n_mu;
+  const long long total = rows * d.n_s;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+  k_deriv<<<blocks, 256, 0, (cudaStream_t)stream>>>(in, out, rows, d.n_s, (float)(1.0 / d.ds), kind);
+  DC_CHECK_LAUNCH("k_deriv");
+  return DC_OK;
+}
+
 // Test hook of the timeout path: one thread waits, with the library's bound
 // (~2^31 cycles), on an mbarrier that nothing completes, gives up and raises
 // the handle's timeout flag, as a staged kernel does when a copy never lands.

@@ -237,3 +237,16 @@ def test_fine_s_grid_matches_oracle(frac):
     assert rel_l2(_host(gg_g), rg) < 1e-4
     assert rel_l2(_host(gg_W), rW) < 1e-4
     api.dc_sync_status(gg)
+
+
+@pytest.mark.parametrize("kind,fn", [("f", "deriv_f"), ("fT", "deriv_f_T"), ("b", "deriv_b"),
+                                     ("bT", "deriv_b_T")])
+def test_deriv_matches_oracle(prob, kind, fn):
+    case, d = prob["case"], prob["case"].desc
+    rng = np.random.default_rng(41)
+    x = rng.normal(size=(case.B, d["n_views"], d["n_mu"], d["n_s"])).astype(np.float32)
+    got = _host(api.dc_deriv(prob["gpu"], _dev(x), kind))
+    for b in range(case.B):
+        for i in range(d["n_views"]):
+            ref = getattr(orc, fn)(x[b, i], d["ds"])
+            assert rel_l2(got[b, i], ref) < 1e-6
