@@ -161,6 +161,21 @@ int dc_filter_adjoint(const dc_geometry *geom, int B, const float *grad_gF, cons
                       void *stream);
 
 /*
+ * dc_filter_with_s / dc_filter_adjoint_from_s -- the same forward and
+ * reverse mode with Grangeat's function S (Eq. 7) kept in between instead of
+ * recomputed: the forward writes S, [B][V][n_mu][n_s] FP32 device (entry
+ * n_s-1 = 0), as a by-product of the filter; the reverse mode reads it and
+ * skips one line-sum pass over the projections.  Costs B*V*n_mu*n_s floats
+ * of caller memory; the results equal dc_filter / dc_filter_adjoint.
+ * Arguments as there; dc_filter_adjoint_from_s takes S in place of g.
+ */
+int dc_filter_with_s(const dc_geometry *geom, int B, const float *g, const float *W, void *gF,
+                     int dtype, float *gF_scale, float *S, void *stream);
+int dc_filter_adjoint_from_s(const dc_geometry *geom, int B, const float *grad_gF,
+                             const float *S, const float *W, float *grad_g, float *grad_W,
+                             int view_chunk, void *stream);
+
+/*
  * dc_backproject -- voxel-driven cone-beam backprojection of Eq. 5:
  *     f(X) = sum_i bilinear(g^F_i, P_i X) / |X - a_i|^2
  * Pixels outside the detector count as zero; voxels with depth <= 0 in a

@@ -79,6 +79,9 @@ _SIGS = {
     "dc_debug_fail_alloc_after": (None, [ctypes.c_long]),
     "dc_debug_wait_timeout": (ctypes.c_int, [_P, _P]),
     "dc_deriv": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P]),
+    "dc_filter_with_s": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, _P, _P]),
+    "dc_filter_adjoint_from_s": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P,
+                                                ctypes.c_int, _P]),
 }
 
 

@@ -128,8 +128,9 @@ def dc_get_view_geometry(geom: Geometry) -> np.ndarray:
 
 def dc_filter(geom: Geometry, g: torch.Tensor, W: Optional[torch.Tensor] = None,
               dtype: str = "f32", out: Optional[torch.Tensor] = None,
-              scale: Optional[torch.Tensor] = None):
-    """g^F = w_d A2d^T D_b (W K) w_sino D_f A2d w_cos g (Eq. 11).  Returns (g^F, scale)."""
+              scale: Optional[torch.Tensor] = None, S_out: Optional[torch.Tensor] = None):
+    """g^F = w_d A2d^T D_b (W K) w_sino D_f A2d w_cos g (Eq. 11).  Returns (g^F, scale).
+    With S_out ([B, V, n_mu, n_s]) Grangeat's S is kept there for the reverse mode."""
     B = g.shape[0]
     _need(g, "g", torch.float32, (B, geom.V, geom.H, geom.W))
     if W is not None:
@@ -140,28 +141,47 @@ def dc_filter(geom: Geometry, g: torch.Tensor, W: Optional[torch.Tensor] = None,
     _need(out, "gF", tdt, (B, geom.V, geom.H, geom.W))
     if code == DC_F16 and scale is None:
         scale = torch.empty((B, geom.V), device=g.device, dtype=torch.float32)
-    rc = _lib.load().dc_filter(geom.handle, B, _ptr(g), _ptr(W), _ptr(out), code,
-                               _ptr(scale if code == DC_F16 else None), _stream())
-    check(rc, "dc_filter")
+    if S_out is not None:
+        _need(S_out, "S_out", torch.float32, (B, geom.V) + geom.sino_shape)
+        rc = _lib.load().dc_filter_with_s(geom.handle, B, _ptr(g), _ptr(W), _ptr(out), code,
+                                          _ptr(scale if code == DC_F16 else None), _ptr(S_out),
+                                          _stream())
+        check(rc, "dc_filter_with_s")
+    else:
+        rc = _lib.load().dc_filter(geom.handle, B, _ptr(g), _ptr(W), _ptr(out), code,
+                                   _ptr(scale if code == DC_F16 else None), _stream())
+        check(rc, "dc_filter")
     return out, (scale if code == DC_F16 else None)
 
 
-def dc_filter_adjoint(geom: Geometry, grad_gF: torch.Tensor, g: torch.Tensor,
+def dc_filter_adjoint(geom: Geometry, grad_gF: torch.Tensor, g: Optional[torch.Tensor],
                       W: Optional[torch.Tensor] = None, want_grad_g: bool = True,
-                      want_grad_W: bool = True, view_chunk: int = 0):
-    """Reverse mode of dc_filter: returns (dL/dg or None, dL/dW or None)."""
-    B = g.shape[0]
+                      want_grad_W: bool = True, view_chunk: int = 0,
+                      S: Optional[torch.Tensor] = None):
+    """Reverse mode of dc_filter: returns (dL/dg or None, dL/dW or None).
+    With S (kept by dc_filter(..., S_out=...)) g is not needed: the line-sum
+    pass that recomputes S is skipped."""
+    B = grad_gF.shape[0]
     shp = (B, geom.V, geom.H, geom.W)
-    _need(g, "g", torch.float32, shp)
     _need(grad_gF, "grad_gF", torch.float32, shp)
+    if S is not None:
+        _need(S, "S", torch.float32, (B, geom.V) + geom.sino_shape)
+    else:
+        _need(g, "g", torch.float32, shp)
     if W is not None:
         _need(W, "W", torch.float32, (geom.V,) + geom.sino_shape)
-    gg = torch.empty(shp, device=g.device, dtype=torch.float32) if want_grad_g else None
-    gW = (torch.empty((geom.V,) + geom.sino_shape, device=g.device, dtype=torch.float32)
+    dev = grad_gF.device
+    gg = torch.empty(shp, device=dev, dtype=torch.float32) if want_grad_g else None
+    gW = (torch.empty((geom.V,) + geom.sino_shape, device=dev, dtype=torch.float32)
           if want_grad_W else None)
-    rc = _lib.load().dc_filter_adjoint(geom.handle, B, _ptr(grad_gF), _ptr(g), _ptr(W),
-                                       _ptr(gg), _ptr(gW), int(view_chunk), _stream())
-    check(rc, "dc_filter_adjoint")
+    if S is not None:
+        rc = _lib.load().dc_filter_adjoint_from_s(geom.handle, B, _ptr(grad_gF), _ptr(S), _ptr(W),
+                                                  _ptr(gg), _ptr(gW), int(view_chunk), _stream())
+        check(rc, "dc_filter_adjoint_from_s")
+    else:
+        rc = _lib.load().dc_filter_adjoint(geom.handle, B, _ptr(grad_gF), _ptr(g), _ptr(W),
+                                           _ptr(gg), _ptr(gW), int(view_chunk), _stream())
+        check(rc, "dc_filter_adjoint")
     return gg, gW
 
 

@@ -8,9 +8,10 @@ trainable layer:
 forward  -> dc_filter, dc_backproject (optional ReLU)
 backward -> dc_backproject_adjoint (masked by the ReLU), dc_filter_adjoint
 
-Nothing but g, W and (with ReLU) the output volume is kept between the
-passes: the filter adjoint recomputes Grangeat's function S view-chunk by
-view-chunk, so training memory is two projection sets and the volumes.
+Between the passes the forward keeps Grangeat's function S (cache_s, the
+default: the backward then skips the line-sum pass that would recompute
+it), or only g (cache_s=False: S is recomputed view-chunk by view-chunk),
+plus W and, with ReLU, the output volume.
 """
 from __future__ import annotations
 
@@ -22,42 +23,58 @@ from . import api
 
 
 class DefriseClackFunction(torch.autograd.Function):
-    """f = A3d^T filter(g, W) with gradients for g and W."""
+    """f = A3d^T filter(g, W) with gradients for g and W.
+
+    cache_s keeps Grangeat's function S from the forward pass (B*V*n_mu*n_s
+    floats) so that the backward skips the line-sum pass that recomputes it;
+    without it only g is kept."""
 
     @staticmethod
     def forward(ctx, g: torch.Tensor, W: Optional[torch.Tensor], geom: api.Geometry,
-                relu: bool = False, view_chunk: int = 0):
+                relu: bool = False, view_chunk: int = 0, cache_s: bool = True):
         g = g.contiguous()
         Wc = None if W is None else W.contiguous()
-        gF, _ = api.dc_filter(geom, g, Wc)
+        need_grad = ctx.needs_input_grad[0] or ctx.needs_input_grad[1]
+        S = None
+        if cache_s and need_grad:
+            S = torch.empty((g.shape[0], geom.V) + geom.sino_shape, device=g.device,
+                            dtype=torch.float32)
+        gF, _ = api.dc_filter(geom, g, Wc, S_out=S)
         vol = api.dc_backproject(geom, gF, relu=relu)
         del gF
         ctx.geom = geom
         ctx.relu = relu
         ctx.view_chunk = view_chunk
         ctx.has_W = W is not None
-        ctx.save_for_backward(g, Wc if Wc is not None else g.new_empty(0),
+        ctx.has_S = S is not None
+        ctx.save_for_backward(S if S is not None else g,
+                              Wc if Wc is not None else g.new_empty(0),
                               vol if relu else g.new_empty(0))
         return vol
 
     @staticmethod
     def backward(ctx, grad_vol: torch.Tensor):
-        g, W, vol = ctx.saved_tensors
+        kept, W, vol = ctx.saved_tensors
         W = W if ctx.has_W else None
         relu_vol = vol if ctx.relu else None
         need_g, need_W = ctx.needs_input_grad[0], ctx.needs_input_grad[1] and ctx.has_W
         if not (need_g or need_W):
-            return None, None, None, None, None
+            return None, None, None, None, None, None
         grad_gF = api.dc_backproject_adjoint(ctx.geom, grad_vol.contiguous(), relu_vol)
-        gg, gW = api.dc_filter_adjoint(ctx.geom, grad_gF, g, W, want_grad_g=need_g,
-                                       want_grad_W=need_W, view_chunk=ctx.view_chunk)
-        return gg, gW, None, None, None
+        if ctx.has_S:
+            gg, gW = api.dc_filter_adjoint(ctx.geom, grad_gF, None, W, want_grad_g=need_g,
+                                           want_grad_W=need_W, view_chunk=ctx.view_chunk,
+                                           S=kept)
+        else:
+            gg, gW = api.dc_filter_adjoint(ctx.geom, grad_gF, kept, W, want_grad_g=need_g,
+                                           want_grad_W=need_W, view_chunk=ctx.view_chunk)
+        return gg, gW, None, None, None, None
 
 
 def reconstruct(g: torch.Tensor, W: Optional[torch.Tensor], geom: api.Geometry,
-                relu: bool = False, view_chunk: int = 0) -> torch.Tensor:
+                relu: bool = False, view_chunk: int = 0, cache_s: bool = True) -> torch.Tensor:
     """Differentiable Eq. 12 (see DefriseClackFunction)."""
-    return DefriseClackFunction.apply(g, W, geom, relu, view_chunk)
+    return DefriseClackFunction.apply(g, W, geom, relu, view_chunk, cache_s)
 
 
 class GaussSmoothFunction(torch.autograd.Function):
@@ -92,12 +109,14 @@ class DefriseClackNet(torch.nn.Module):
     """
 
     def __init__(self, geom: api.Geometry, init=0.5, relu: bool = True,
-                 view_chunk: int = 0, device=None, smooth=None, seed: int = 0):
+                 view_chunk: int = 0, device=None, smooth=None, seed: int = 0,
+                 cache_s: bool = True):
         super().__init__()
         self.geom = geom
         self.relu = relu
         self.view_chunk = view_chunk
         self.smooth = smooth
+        self.cache_s = cache_s
         shape = (geom.V,) + geom.sino_shape
         if init == "uniform":
             gen = torch.Generator(device="cpu").manual_seed(seed)
@@ -111,4 +130,5 @@ class DefriseClackNet(torch.nn.Module):
         return gauss_smooth(self.W, *self.smooth) if self.smooth else self.W
 
     def forward(self, g: torch.Tensor) -> torch.Tensor:
-        return reconstruct(g, self.weights(), self.geom, self.relu, self.view_chunk)
+        return reconstruct(g, self.weights(), self.geom, self.relu, self.view_chunk,
+                           self.cache_s)

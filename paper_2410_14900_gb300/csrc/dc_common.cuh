@@ -45,6 +45,7 @@ enum KernelId {
   KID_BP3D,
   KID_BP3D_ADJ,
   KID_SMOOTH,
+  KID_ADJ_S,
   KID_COUNT
 };
 
@@ -168,8 +169,10 @@ int filter_check(const dc_geometry *g, int B, const float *gin, const void *gF, 
 // chunk sizes: bc batch items of cv views per chunk of the work area
 void filter_chunk_plan(const dc_geometry *g, int B, int *bc, int *cv);
 // the filter of one chunk: views [v0, v0 + nv) of items [b0, b0 + bc)
+// (S: optional [B][V][n_mu][n_s] copy of Grangeat's function, or NULL)
 int filter_chunk(const dc_geometry *g, const float *gin, const float *W, void *gF, int dtype,
-                 float *gF_scale, int b0, int bc, int v0, int nv, cudaStream_t st);
+                 float *gF_scale, int b0, int bc, int v0, int nv, cudaStream_t st,
+                 float *S = nullptr);
 // checks of dc_backproject's arguments
 int backproject_check(const dc_geometry *g, int B, const void *gF, int dtype,
                       const float *gF_scale, const float *vol, unsigned flags, const char *who);

@@ -105,6 +105,7 @@ struct LineArgs {
   float *out;          // RAW/GRANGEAT: user [B][V][n_mu][n_s]; else scratch [n][n_mu][NSp]
   float *sinoA;        // DIFFSTORE out / ADJ in-out (scratch)
   float *sinoB;        // ADJ out (scratch)
+  float *Sout;         // FILTER: optional copy of S, user [B][V][n_mu][n_s]
   unsigned *err;
   int mg;              // max angles per group
 };
@@ -117,6 +118,20 @@ struct LineMu {
   float dxi;         // -sn/cs as a float
   float jscale;      // p / |cs|
 };
+
+// half-grid abscissa s_{k+1/2} and the weight K = -(1/4pi^2)|v.theta| / (s^2 +
+// D^2) of Eq. 10 on it (theta unnormalised: the norm is folded into the
+// denominator); shared by the line-sum epilogues and the cached-S adjoint so
+// that both give the same FP32 values
+__device__ __forceinline__ float s_half_of(int k, int n_s, float ds) {
+  return ((float)k - 0.5f * (float)(n_s - 1) + 0.5f) * ds;
+}
+__device__ __forceinline__ float redundancy_k(const dc::MuRec &r, const dc::FView &fv, float sh) {
+  const float D = fv.D, D2 = D * D;
+  const float inv4pi2 = 1.0f / (4.0f * kPi * kPi);
+  const float vt = fmaf(sh, fv.az, D * fmaf(r.c, fv.ax, r.s * fv.ay));
+  return -fabsf(vt) * inv4pi2 / fmaf(sh, sh, D2);
+}
 
 // Joseph sum of one line over the nr steps of a staged band: the sample at
 // step q sits at fb + q*dxi samples from the band anchor and is interpolated
@@ -286,14 +301,9 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
   __syncthreads();
 
   const float D = fv.D, D2 = D * D;
-  const float inv4pi2 = 1.0f / (4.0f * kPi * kPi);
   const int total = G.count * a.NSp;
-  auto s_half = [&](int k) { return ((float)k - 0.5f * (float)(a.n_s - 1) + 0.5f) * a.ds; };
-  auto Kw = [&](int m, float sh) {  // -(1/4pi^2)|v.theta|/sqrt(s^2+D^2)
-    const dc::MuRec r = a.mu[m];
-    float vt = fmaf(sh, fv.az, D * fmaf(r.c, fv.ax, r.s * fv.ay));
-    return -fabsf(vt) * inv4pi2 / fmaf(sh, sh, D2);
-  };
+  auto s_half = [&](int k) { return s_half_of(k, a.n_s, a.ds); };
+  auto Kw = [&](int m, float sh) { return redundancy_k(a.mu[m], fv, sh); };
 
   if (MODE == M_RAW || MODE == M_GRANGEAT) {
     for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
@@ -329,6 +339,12 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
         float sh = s_half(k);
         float w = a.Wred ? a.Wred[((size_t)v * a.n_mu + m) * a.n_s + k] : 0.5f;
         q = w * Kw(m, sh) * (fmaf(sh, sh, D2) / D2) * ep[idx] / a.ds;
+        // Grangeat's S (Eq. 7), kept for a reverse mode that reuses it
+        if (a.Sout)
+          a.Sout[(((size_t)b * a.V + v) * a.n_mu + m) * a.n_s + k] =
+              ep[idx] * (fmaf(sh, sh, D2) / D2) / a.ds;
+      } else if (a.Sout && k < a.n_s) {
+        a.Sout[(((size_t)b * a.V + v) * a.n_mu + m) * a.n_s + k] = 0.0f;
       }
       ep[idx] = q;
     }
@@ -687,6 +703,52 @@ __global__ void k_sino_in(const float *__restrict__ R, const dc::MuRec *__restri
 
 int round4(int x) { return (x + 3) & ~3; }
 
+// The last step of the filter's reverse mode with Grangeat's S read from
+// memory (kept by the forward pass) instead of recomputed by a line-sum
+// pass: the same arithmetic as the M_ADJ epilogue of k_linesum.  A CTA
+// takes AS_ROWS angles of one image; sinoA holds jscale (R_G[k+1] - R_G[k])
+// of w_d dL/dg^F on entry and dL/dW contributions on exit, sinoB receives
+// D_f^T of dL/dS (times the Joseph scale) for the 2-D backprojection.
+constexpr int AS_ROWS = 4;
+
+__global__ void __launch_bounds__(256) k_adj_from_s(LineArgs a, const float *__restrict__ S) {
+  extern __shared__ float ys[];  // [AS_ROWS][NSp]
+  const int n = blockIdx.y;
+  const int v = a.v0 + n / a.B, b = a.b0 + n % a.B;
+  const dc::FView fv = a.fv[v];
+  const float D = fv.D, D2 = D * D;
+  const int m0 = blockIdx.x * AS_ROWS;
+  const int total = min(AS_ROWS, a.n_mu - m0) * a.NSp;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int m = m0 + idx / a.NSp, k = idx % a.NSp;
+    const size_t o = ((size_t)n * a.n_mu + m) * a.NSp + k;
+    float y = 0.0f, tW = 0.0f;
+    if (k <= a.n_s - 2) {
+      const float sh = s_half_of(k, a.n_s, a.ds);
+      const float wsino = fmaf(sh, sh, D2) / D2;
+      const float Sv = S[(((size_t)b * a.V + v) * a.n_mu + m) * a.n_s + k];
+      const float Qg = -a.cT * a.sinoA[o] / a.ds;  // D_b^T of dL/dP
+      const float Kv = redundancy_k(a.mu[m], fv, sh);
+      const float w = a.Wred ? a.Wred[((size_t)v * a.n_mu + m) * a.n_s + k] : 0.5f;
+      tW = Kv * Sv * Qg;
+      y = wsino * w * Kv * Qg;
+    }
+    a.sinoA[o] = tW;
+    ys[idx] = y;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int m = m0 + idx / a.NSp, k = idx % a.NSp;
+    float val = 0.0f;
+    if (k < a.n_s) {
+      const float ym = (k > 0) ? ys[idx - 1] : 0.0f;
+      const float y0 = (k <= a.n_s - 2) ? ys[idx] : 0.0f;
+      val = (ym - y0) / a.ds * a.mu[m].jscale;
+    }
+    a.sinoB[((size_t)n * a.n_mu + m) * a.NSp + k] = val;
+  }
+}
+
 size_t linesum_smem_for(int H, int W, int mg, int NSp, int rb) {
   return (size_t)(2 * (std::max(H, W) + 2 * (rb + 1)) * (rb + 1) + mg * NSp) * sizeof(float);
 }
@@ -911,7 +973,7 @@ void filter_chunk_plan(const dc_geometry *g, int B, int *bc, int *cv) {
 
 // the filter of images (view v0 + n / bc, item b0 + n % bc), n < nv * bc
 int filter_chunk(const dc_geometry *g, const float *gin, const float *W, void *gF, int dtype,
-                 float *gF_scale, int b0, int bc, int v0, int nv, cudaStream_t st) {
+                 float *gF_scale, int b0, int bc, int v0, int nv, cudaStream_t st, float *S) {
   const dc_geometry_desc &d = g->d;
   const int n_img = nv * bc;
   int rc;
@@ -919,6 +981,7 @@ int filter_chunk(const dc_geometry *g, const float *gin, const float *W, void *g
   LineArgs la = line_args(g, bc, v0, b0, n_img);
   la.Wred = W;
   la.out = g->w_sinoA;
+  la.Sout = S;
   if ((rc = launch_linesum<M_FILTER>(g, la, st))) return rc;
   BP2Args ba = bp2_args(g, bc, v0, b0, n_img, g->w_sinoA);
   ba.weight = WT_D;
@@ -948,9 +1011,9 @@ extern "C" {
 // the outer loop takes bc batch items starting at b0, the inner loop cv views
 // starting at v0; image n of a chunk is (view v0 + n / bc, item b0 + n % bc).
 
-int dc_filter(const dc_geometry *g, int B, const float *gin, const float *W, void *gF,
-              int dtype, float *gF_scale, void *stream) {
-  int rc = dc::filter_check(g, B, gin, gF, dtype, gF_scale, "dc_filter");
+static int filter_all(const dc_geometry *g, int B, const float *gin, const float *W, void *gF,
+                      int dtype, float *gF_scale, float *S, void *stream, const char *who) {
+  int rc = dc::filter_check(g, B, gin, gF, dtype, gF_scale, who);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   int bcm, cvm;
@@ -959,10 +1022,22 @@ int dc_filter(const dc_geometry *g, int B, const float *gin, const float *W, voi
     int bc = std::min(bcm, B - b0);
     for (int v0 = 0; v0 < g->d.n_views; v0 += cvm) {
       int nv = std::min(cvm, g->d.n_views - v0);
-      if ((rc = dc::filter_chunk(g, gin, W, gF, dtype, gF_scale, b0, bc, v0, nv, st))) return rc;
+      if ((rc = dc::filter_chunk(g, gin, W, gF, dtype, gF_scale, b0, bc, v0, nv, st, S)))
+        return rc;
     }
   }
   return DC_OK;
+}
+
+int dc_filter(const dc_geometry *g, int B, const float *gin, const float *W, void *gF,
+              int dtype, float *gF_scale, void *stream) {
+  return filter_all(g, B, gin, W, gF, dtype, gF_scale, nullptr, stream, "dc_filter");
+}
+
+int dc_filter_with_s(const dc_geometry *g, int B, const float *gin, const float *W, void *gF,
+                     int dtype, float *gF_scale, float *S, void *stream) {
+  if (!S) return dc::fail(DC_ERR_ARG, "dc_filter_with_s: NULL S");
+  return filter_all(g, B, gin, W, gF, dtype, gF_scale, S, stream, "dc_filter_with_s");
 }
 
 int dc_filter_adjoint(const dc_geometry *g, int B, const float *grad_gF, const float *gin,
@@ -993,6 +1068,58 @@ int dc_filter_adjoint(const dc_geometry *g, int B, const float *grad_gF, const f
       // recompute S from w_cos * g and finish the chain
       if ((rc = launch_prep(g, gin, WT_COS, v0, n_img, bc, b0, st))) return rc;
       if ((rc = launch_linesum<M_ADJ>(g, la, st))) return rc;
+      if (grad_W) {
+        size_t total = (size_t)nv * d.n_mu * d.n_s;
+        int nb = (int)std::min<size_t>((total + 255) / 256, 4096);
+        dc::ProfScope ps(dc::KID_REDUCE_W, st);
+        k_reduce_gradW<<<nb, 256, 0, st>>>(g->w_sinoA, d.n_mu, d.n_s, g->NSp, bc, v0, nv,
+                                           b0 > 0, grad_W);
+        DC_CHECK_LAUNCH("k_reduce_gradW");
+      }
+      if (grad_g) {
+        BP2Args ba = bp2_args(g, bc, v0, b0, n_img, g->w_sinoB);
+        ba.weight = WT_COS;
+        ba.out_kind = OUT_F32;
+        ba.out = grad_g;
+        if ((rc = launch_bp2d(g, ba, st))) return rc;
+      }
+    }
+  }
+  return DC_OK;
+}
+
+int dc_filter_adjoint_from_s(const dc_geometry *g, int B, const float *grad_gF,
+                             const float *S, const float *W, float *grad_g, float *grad_W,
+                             int view_chunk, void *stream) {
+  int rc = check_common(g, B, "dc_filter_adjoint_from_s");
+  if (rc) return rc;
+  if (!grad_gF || !S)
+    return dc::fail(DC_ERR_ARG, "dc_filter_adjoint_from_s: NULL grad_gF or S");
+  if (view_chunk < 0) return dc::fail(DC_ERR_ARG, "dc_filter_adjoint_from_s: negative view_chunk");
+  const dc_geometry_desc &d = g->d;
+  if (3.0 * d.ds < d.pitch * (1.0 - 1e-12))
+    return dc::fail(DC_ERR_UNSUPPORTED, "dc_filter_adjoint_from_s: ds < pitch/3 is not supported");
+  if (!grad_g && !grad_W) return DC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Chunking ck = chunking(g, B, view_chunk);
+  for (int b0 = 0; b0 < B; b0 += ck.bc) {
+    int bc = std::min(ck.bc, B - b0);
+    for (int v0 = 0; v0 < d.n_views; v0 += ck.cv) {
+      int nv = std::min(ck.cv, d.n_views - v0);
+      int n_img = nv * bc;
+      // dL/dP up to D_b^T: line differences of w_d * dL/dg^F
+      if ((rc = launch_prep(g, grad_gF, WT_D, v0, n_img, bc, b0, st))) return rc;
+      LineArgs la = line_args(g, bc, v0, b0, n_img);
+      la.Wred = W;
+      la.sinoA = g->w_sinoA;
+      la.sinoB = g->w_sinoB;
+      if ((rc = launch_linesum<M_DIFFSTORE>(g, la, st))) return rc;
+      {  // finish the chain with the stored S
+        dim3 grid((d.n_mu + AS_ROWS - 1) / AS_ROWS, n_img);
+        dc::ProfScope ps(dc::KID_ADJ_S, st);
+        k_adj_from_s<<<grid, 256, sizeof(float) * AS_ROWS * g->NSp, st>>>(la, S);
+        DC_CHECK_LAUNCH("k_adj_from_s");
+      }
       if (grad_W) {
         size_t total = (size_t)nv * d.n_mu * d.n_s;
         int nb = (int)std::min<size_t>((total + 255) / 256, 4096);

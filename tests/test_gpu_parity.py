@@ -250,3 +250,21 @@ def test_deriv_matches_oracle(prob, kind, fn):
         for i in range(d["n_views"]):
             ref = getattr(orc, fn)(x[b, i], d["ds"])
             assert rel_l2(got[b, i], ref) < 1e-6
+
+
+def test_kept_grangeat_function_gives_the_same_filter_and_gradients(prob):
+    """dc_filter_with_s keeps S (equal to dc_grangeat's) and leaves g^F
+    unchanged; dc_filter_adjoint_from_s gives dc_filter_adjoint's gradients."""
+    case, d = prob["case"], prob["case"].desc
+    g, W = _dev(prob["g"]), _dev(prob["W"])
+    S = torch.empty((case.B, d["n_views"], d["n_mu"], d["n_s"]), device="cuda")
+    gF1, _ = api.dc_filter(prob["gpu"], g, W)
+    gF2, _ = api.dc_filter(prob["gpu"], g, W, S_out=S)
+    assert torch.equal(gF1, gF2)
+    S_ref = api.dc_grangeat(prob["gpu"], g)
+    assert torch.equal(S, S_ref)
+    G = _dev(np.random.default_rng(51).normal(size=prob["g"].shape))
+    gg1, gW1 = api.dc_filter_adjoint(prob["gpu"], G, g, W)
+    gg2, gW2 = api.dc_filter_adjoint(prob["gpu"], G, None, W, S=S)
+    torch.cuda.synchronize()
+    assert torch.equal(gg1, gg2) and torch.equal(gW1, gW2)
