@@ -57,6 +57,8 @@ extern "C" {
 #define DC_ERR_OOM 3          /* device allocation failed                   */
 #define DC_ERR_TIMEOUT 4      /* a bounded device wait gave up              */
 #define DC_ERR_UNSUPPORTED 5  /* valid request this build does not handle  */
+#define DC_ERR_NONFINITE 6    /* a NaN / infinite redundancy weight was read
+                                 (reported by dc_sync_status)               */
 
 /* storage types of the filtered projections g^F */
 #define DC_F32 0
@@ -321,9 +323,11 @@ int dc_radon2d_adjoint(const dc_geometry *geom, int B, const float *R, float *im
 /*
  * dc_sync_status -- waits for `stream`, then reports device-side failures of
  * this handle's kernels since the last call: DC_ERR_TIMEOUT if a bounded
- * wait inside a kernel gave up (the kernel then skipped its output).  Clears
- * the flag.  Compute calls never block, so they cannot report this
- * themselves.
+ * wait inside a kernel gave up (the kernel then skipped its output), else
+ * DC_ERR_NONFINITE if a filter call (forward or reverse mode) read a NaN or
+ * infinite redundancy weight W (the outputs that depend on that weight are
+ * then NaN; no other output is affected).  Clears the flags.  Compute calls
+ * never block, so they cannot report these themselves.
  */
 int dc_sync_status(const dc_geometry *geom, void *stream);
 
@@ -334,6 +338,9 @@ int dc_sync_status(const dc_geometry *geom, void *stream);
  *   kind 1: D_f^T
  *   kind 2: D_b, out[k] = (in[k] - in[k-1]) / ds with in[-1] = 0
  *   kind 3: D_b^T
+ * Each difference is divided by ds in FP32, as in the filter's fused
+ * derivatives; the results agree with those to FP32 rounding (the fused
+ * path differences per-band partial line sums).
  */
 int dc_deriv(const dc_geometry *geom, int B, const float *in, float *out, int kind,
              void *stream);
@@ -351,13 +358,16 @@ int dc_deriv(const dc_geometry *geom, int B, const float *in, float *out, int ki
  *   R     : device, [n_img][n_mu][n_s] FP32 line sums (caller-owned).
  *   cu, cv: principal point (column, row) shared by all images; pitch, ds,
  *           mu_m = m pi / n_mu and s_k as for a geometry handle.
- * Limits: n_mu <= 2048; one image needs (H * round4(W) + W * round4(H)) * 4
- * bytes of the fixed area, at most 32 MiB - 256 KiB (larger requests return
- * DC_ERR_ARG with the numbers); images are processed in groups that fit.
- * The first call on a device looks up the array's device address (set-up);
- * make that first call before any stream capture.  All calls share the array
- * and it keeps the last call's contents: calls that overlap on the GPU (two
- * streams, two threads) race on it and must be serialised by the caller.
+ * Limits: n_mu <= 2048; one image needs H * round4(W) * 4 bytes of the fixed
+ * area (its weighted copy with rows padded to a multiple of 4 floats), at
+ * most 32 MiB - 256 KiB (larger requests return DC_ERR_ARG with the
+ * numbers); images are processed in groups that fit.
+ * The first call on a device (and the first after that device's context
+ * changed, e.g. after cudaDeviceReset) looks up the array's device address
+ * (set-up); make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents: calls that overlap on the
+ * GPU (two streams, two threads) race on it and must be serialised by the
+ * caller.
  */
 int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, double pitch, double ds,
                        double cu, double cv, const float *img, float *R, void *stream);

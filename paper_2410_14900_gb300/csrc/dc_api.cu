@@ -98,6 +98,7 @@ const char *dc_status_string(int status) {
     case DC_ERR_CUDA: return "DC_ERR_CUDA: CUDA call failed";
     case DC_ERR_OOM: return "DC_ERR_OOM: device allocation failed";
     case DC_ERR_TIMEOUT: return "DC_ERR_TIMEOUT: bounded device wait gave up";
+    case DC_ERR_NONFINITE: return "DC_ERR_NONFINITE: NaN or infinite redundancy weight";
     case DC_ERR_UNSUPPORTED: return "DC_ERR_UNSUPPORTED: not supported by this build";
     default: return "unknown status";
   }

@@ -9,6 +9,10 @@
 
 #include "../../include/dracogb.h"
 
+// bits of a handle's device-side error word (w_flags[0])
+#define DC_FLAG_TIMEOUT 1u        // a bounded wait gave up (the kernel skipped its output)
+#define DC_FLAG_NONFINITE_W 2u    // a redundancy weight read by a filter kernel was NaN / inf
+
 namespace dc {
 
 // ---------------------------------------------------------------- errors

@@ -19,6 +19,7 @@
 //               of every angle (the exact transpose of the Joseph weights),
 //               angles streamed through shared memory with bulk copies; the
 //               epilogue applies w_d (forward) or w_cos (adjoint)
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -331,6 +332,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
   }
   if (MODE == M_FILTER) {
     // Q = W K w_sino (R_{k+1}-R_k)/ds on s_{k+1/2}
+    bool bad_w = false;
     for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
       int ml = idx / a.NSp, k = idx % a.NSp;
       int m = a.mu_order[G.first + ml];
@@ -338,6 +340,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
       if (k <= a.n_s - 2) {
         float sh = s_half(k);
         float w = a.Wred ? a.Wred[((size_t)v * a.n_mu + m) * a.n_s + k] : 0.5f;
+        bad_w |= !isfinite(w);
         q = w * Kw(m, sh) * (fmaf(sh, sh, D2) / D2) * ep[idx] / a.ds;
         // Grangeat's S (Eq. 7), kept for a reverse mode that reuses it
         if (a.Sout)
@@ -348,6 +351,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
       }
       ep[idx] = q;
     }
+    if (bad_w) atomicOr(a.err, DC_FLAG_NONFINITE_W);
     __syncthreads();
     // P = D_b Q, times the A2d^T scale (pi/n_mu)(ds/p^2) and the Joseph scale
     for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
@@ -365,6 +369,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
   if (MODE == M_ADJ) {
     // sinoA holds jscale*(R_G[k+1]-R_G[k]) of w_d*dL/dg^F; this launch's
     // line differences are those of w_cos*g (Grangeat's S, recomputed).
+    bool bad_w = false;
     for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
       int ml = idx / a.NSp, k = idx % a.NSp;
       int m = a.mu_order[G.first + ml];
@@ -377,12 +382,14 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
         float Qg = -a.cT * a.sinoA[o] / a.ds;  // D_b^T of dL/dP
         float Kv = Kw(m, sh);
         float w = a.Wred ? a.Wred[((size_t)v * a.n_mu + m) * a.n_s + k] : 0.5f;
+        bad_w |= !isfinite(w);
         tW = Kv * S * Qg;                       // dL/dW contribution
         y = wsino * w * Kv * Qg;                // dL/dS times w_sino
       }
       a.sinoA[o] = tW;
       ep[idx] = y;
     }
+    if (bad_w) atomicOr(a.err, DC_FLAG_NONFINITE_W);
     __syncthreads();
     // dL/dR = D_f^T y; times the Joseph scale for the transpose gather
     for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
@@ -436,17 +443,6 @@ struct BPMu {
   int row0;                 // float offset of s-bin I00 in its stage
   int pad1, pad2;
 };
-
-// the two sinogram taps around s-bin position x (relative to a row anchor
-// folded into cb, as in band_sum) and the fraction of x past the first
-__device__ __forceinline__ float taps(const char *sb, unsigned cb, float x, float &p0, float &p1) {
-  const float M = 12582912.0f;
-  const float t = __fadd_rd(x, M);
-  const unsigned off = __float_as_uint(t) * 4u + cb;
-  p0 = *reinterpret_cast<const float *>(sb + off);
-  p1 = *reinterpret_cast<const float *>(sb + off + 4);
-  return x - (t - M);
-}
 
 // MULTI: ds < pitch, where the transposed Joseph hat of an angle (half-width
 // 1/winv s-bins, at most 3 for ds >= pitch/3) covers up to six taps; those
@@ -524,17 +520,24 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
   }
   angle_consts(0);
 
-  float acc[BP2_RY][BP2_NQ];
+  // a thread's two pixels of a row (columns lane and lane + 32) are held as
+  // the two halves of a float2 and stepped with the packed FP32x2 operations
+  // of sm_100+ (one issue slot for both); every component is rounded as the
+  // scalar operation would round it
+  static_assert(BP2_NQ == 2, "two pixels per thread and row, packed");
+  float2 acc[BP2_RY];
 #pragma unroll
-  for (int ry = 0; ry < BP2_RY; ++ry)
-#pragma unroll
-    for (int q = 0; q < BP2_NQ; ++q) acc[ry][q] = 0.0f;
+  for (int ry = 0; ry < BP2_RY; ++ry) acc[ry] = make_float2(0.0f, 0.0f);
   const float rl0 = (float)(warp * BP2_RY);
   float jlf[BP2_NQ], rlf[BP2_RY];  // pixel offsets inside the tile, as floats
 #pragma unroll
   for (int q = 0; q < BP2_NQ; ++q) jlf[q] = (float)(lane + 32 * q);
 #pragma unroll
   for (int ry = 0; ry < BP2_RY; ++ry) rlf[ry] = rl0 + (float)ry;
+  const float2 jl2 = make_float2(jlf[0], jlf[1]);
+  const float2 mM2 = make_float2(-12582912.0f, -12582912.0f);  // -1.5 * 2^23
+  const float2 M2 = make_float2(12582912.0f, 12582912.0f);
+  const float2 m12 = make_float2(-1.0f, -1.0f);
 
   bool ok = true;
   for (int c = 0; c < nchunk; ++c) {
@@ -569,35 +572,34 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
               const float w = fmaxf(0.0f, fmaf(-fabsf(f - (float)t), M.winv, 1.0f));
               if (kk >= klo && kk <= khi) sum = fmaf(w, row[kk], sum);
             }
-            acc[ry][q] += sum;
-          }
-        }
-      } else if (M.fast) {
-#pragma unroll
-        for (int ry = 0; ry < BP2_RY; ++ry) {
-          float rt = fmaf(rlf[ry], M.Bs, M.F00);
-#pragma unroll
-          for (int q = 0; q < BP2_NQ; ++q) {
-            float p0, p1;
-            const float f = taps(sb, cb, fmaf(jlf[q], M.Bc, rt), p0, p1);
-            float w0 = fmaxf(0.0f, fmaf(-f, M.winv, 1.0f));
-            float w1 = fmaxf(0.0f, fmaf(f, M.winv, M.w1c));
-            acc[ry][q] = fmaf(w0, p0, fmaf(w1, p1, acc[ry][q]));
+            if (q == 0) acc[ry].x += sum;
+            else acc[ry].y += sum;
           }
         }
       } else {
+        // two-tap paths (ds >= pitch, so winv >= 1): the hat weights
+        // 1 - f winv and 1 - (1 - f) winv never exceed 1, so clamping them
+        // below at 0 is a saturation to [0, 1]
+        const float2 Bc2 = make_float2(M.Bc, M.Bc);
 #pragma unroll
         for (int ry = 0; ry < BP2_RY; ++ry) {
-          float rt = fmaf(rlf[ry], M.Bs, M.F00);
-#pragma unroll
-          for (int q = 0; q < BP2_NQ; ++q) {
-            float p0, p1;
-            const float f =
-                taps(sb, cb, fminf(fmaxf(fmaf(jlf[q], M.Bc, rt), M.lo), M.hi), p0, p1);
-            float w0 = fmaxf(0.0f, fmaf(-f, M.winv, 1.0f));
-            float w1 = fmaxf(0.0f, fmaf(f, M.winv, M.w1c));
-            acc[ry][q] = fmaf(w0, p0, fmaf(w1, p1, acc[ry][q]));
-          }
+          const float rt = fmaf(rlf[ry], M.Bs, M.F00);
+          float2 x = __ffma2_rn(jl2, Bc2, make_float2(rt, rt));
+          if (!M.fast)
+            x = make_float2(fminf(fmaxf(x.x, M.lo), M.hi), fminf(fmaxf(x.y, M.lo), M.hi));
+          // exact floor (rounded-down bits) and fraction, as in band_sum
+          const float2 t = __fadd2_rd(x, M2);
+          const float2 f = __ffma2_rn(__fadd2_rn(t, mM2), m12, x);
+          const unsigned o0 = __float_as_uint(t.x) * 4u + cb, o1 = __float_as_uint(t.y) * 4u + cb;
+          const float2 p0 = make_float2(*reinterpret_cast<const float *>(sb + o0),
+                                        *reinterpret_cast<const float *>(sb + o1));
+          const float2 p1 = make_float2(*reinterpret_cast<const float *>(sb + o0 + 4),
+                                        *reinterpret_cast<const float *>(sb + o1 + 4));
+          const float2 w0 = make_float2(__saturatef(fmaf(-f.x, M.winv, 1.0f)),
+                                        __saturatef(fmaf(-f.y, M.winv, 1.0f)));
+          const float2 w1 = make_float2(__saturatef(fmaf(f.x, M.winv, M.w1c)),
+                                        __saturatef(fmaf(f.y, M.winv, M.w1c)));
+          acc[ry] = __ffma2_rn(w0, p0, __ffma2_rn(w1, p1, acc[ry]));
         }
       }
     }
@@ -617,7 +619,7 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
     for (int q = 0; q < BP2_NQ; ++q) {
       int j = j0 + lane + 32 * q;
       if (r >= a.H || j >= a.W) continue;
-      float val = acc[ry][q];
+      float val = (q == 0) ? acc[ry].x : acc[ry].y;
       if (a.weight != WT_NONE) {
         float x = (j - fv.cu) * a.pitch, y = (r - fv.cv) * a.pitch;
         float l2 = fmaf(x, x, fmaf(y, y, fv.D * fv.D));
@@ -719,6 +721,7 @@ __global__ void __launch_bounds__(256) k_adj_from_s(LineArgs a, const float *__r
   const float D = fv.D, D2 = D * D;
   const int m0 = blockIdx.x * AS_ROWS;
   const int total = min(AS_ROWS, a.n_mu - m0) * a.NSp;
+  bool bad_w = false;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int m = m0 + idx / a.NSp, k = idx % a.NSp;
     const size_t o = ((size_t)n * a.n_mu + m) * a.NSp + k;
@@ -730,12 +733,14 @@ __global__ void __launch_bounds__(256) k_adj_from_s(LineArgs a, const float *__r
       const float Qg = -a.cT * a.sinoA[o] / a.ds;  // D_b^T of dL/dP
       const float Kv = redundancy_k(a.mu[m], fv, sh);
       const float w = a.Wred ? a.Wred[((size_t)v * a.n_mu + m) * a.n_s + k] : 0.5f;
+      bad_w |= !isfinite(w);
       tW = Kv * Sv * Qg;
       y = wsino * w * Kv * Qg;
     }
     a.sinoA[o] = tW;
     ys[idx] = y;
   }
+  if (bad_w) atomicOr(a.err, DC_FLAG_NONFINITE_W);
   __syncthreads();
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int m = m0 + idx / a.NSp, k = idx % a.NSp;
@@ -1213,7 +1218,7 @@ int dc_radon2d_adjoint(const dc_geometry *g, int B, const float *R, float *img, 
 // transpose, 2 D_b (backward difference, zero below k = 0), 3 its transpose;
 // all divided by ds.  One thread per entry, rows read from global memory.
 __global__ void k_deriv(const float *__restrict__ in, float *__restrict__ out, long long rows,
-                        int n_s, float inv_ds, int kind) {
+                        int n_s, float ds, int kind) {
   const long long total = rows * n_s;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -1221,14 +1226,14 @@ __global__ void k_deriv(const float *__restrict__ in, float *__restrict__ out, l
     const float *x = in + (i - k);
     float v;
     if (kind == 0) {
-      v = (k < n_s - 1) ? (x[k + 1] - x[k]) * inv_ds : 0.0f;
+      v = (k < n_s - 1) ? (x[k + 1] - x[k]) / ds : 0.0f;
     } else if (kind == 1) {
       const float a = (k >= 1) ? x[k - 1] : 0.0f, b = (k < n_s - 1) ? x[k] : 0.0f;
-      v = (a - b) * inv_ds;
+      v = (a - b) / ds;
     } else if (kind == 2) {
-      v = (x[k] - (k > 0 ? x[k - 1] : 0.0f)) * inv_ds;
+      v = (x[k] - (k > 0 ? x[k - 1] : 0.0f)) / ds;
     } else {
-      v = (x[k] - (k + 1 < n_s ? x[k + 1] : 0.0f)) * inv_ds;
+      v = (x[k] - (k + 1 < n_s ? x[k + 1] : 0.0f)) / ds;
     }
     out[i] = v;
   }
@@ -1242,8 +1247,10 @@ int dc_deriv(const dc_geometry *g, int B, const float *in, float *out, int kind,
   const dc_geometry_desc &d = g->d;
   const long long rows = (long long)B * d.n_views * d.n_mu;
   const long long total = rows * d.n_s;
-  const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
-  k_deriv<<<blocks, 256, 0, (cudaStream_t)stream>>>(in, out, rows, d.n_s, (float)(1.0 / d.ds), kind);
+  int sms = 0;
+  DC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device));
+  const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)std::max(sms, 1) * 16);
+  k_deriv<<<blocks, 256, 0, (cudaStream_t)stream>>>(in, out, rows, d.n_s, (float)d.ds, kind);
   DC_CHECK_LAUNCH("k_deriv");
   return DC_OK;
 }
@@ -1274,7 +1281,9 @@ int dc_sync_status(const dc_geometry *g, void *stream) {
   DC_CUDA(cudaMemcpy(&flags, g->w_flags, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (flags) {
     DC_CUDA(cudaMemset(g->w_flags, 0, sizeof(unsigned)));
-    return dc::fail(DC_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (flags & DC_FLAG_TIMEOUT) return dc::fail(DC_ERR_TIMEOUT, "a bounded device wait gave up");
+    return dc::fail(DC_ERR_NONFINITE,
+                    "a redundancy weight W read by the filter or its adjoint was NaN or infinite");
   }
   return DC_OK;
 }
@@ -1304,9 +1313,28 @@ static_assert((sizeof(dc::MuRec) + sizeof(dc::VMu) + sizeof(int) + sizeof(dc::Mu
 
 static __device__ __align__(256) unsigned char g_na_scratch[NA_BYTES];
 
-// set-up: the device address of g_na_scratch, once per device
+// set-up: the device address of g_na_scratch, once per device and context
+// (a cudaDeviceReset gives the device a new primary context in which the
+// array has a new address, so the cache is keyed on the current context)
 void *g_na_ptr[NA_MAX_DEV];
+void *g_na_ctx[NA_MAX_DEV];
 std::mutex g_na_mu;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+CtxGetCurrentFn ctx_get_current_fn() {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)p;
+    looked = true;
+  }
+  return fn;
+}
 
 // Angle tables for one call, written into the fixed area: one thread per
 // angle for the per-angle records, thread 0 for the ordering and grouping
@@ -1381,11 +1409,15 @@ extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, do
   unsigned char *base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    CUcontext ctx = nullptr;
+    CtxGetCurrentFn cur = ctx_get_current_fn();
+    if (cur && cur(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+    if (!g_na_ptr[dev] || (ctx && ctx != (CUcontext)g_na_ctx[dev])) {
       void *p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
       if (e != cudaSuccess) return dc::cuda_fail(e, "cudaGetSymbolAddress(g_na_scratch)");
       g_na_ptr[dev] = p;
+      g_na_ctx[dev] = (void *)ctx;
     }
     base = (unsigned char *)g_na_ptr[dev];
   }

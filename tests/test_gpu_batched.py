@@ -1,10 +1,12 @@
 """Batched reconstruction (one persistent backprojection over uneven
-problems) and its CUDA-graph capture: the same volumes as the per-problem
-calls, which the other tests compare with the oracle."""
+problems) and its CUDA-graph capture: every volume against the FP64 oracle's
+reconstruction of its own problem (Eq. 12), and against the per-problem
+calls."""
 import numpy as np
 import pytest
 import torch
 
+from oracle import oracle as orc
 from paper_2410_14900_gb300 import api, synth, tune
 
 from cases import rel_l2
@@ -22,6 +24,35 @@ def _problems():
                                   device="cuda", dtype=torch.float32).contiguous()
         out.append((w, geom, g))
     return out
+
+
+# FP32: the method's 1e-4 target; BF16 / FP16 storage of g^F: the stated
+# storage error of those forms (measured ~7e-4 and ~1e-4 on these problems)
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-4), ("bf16", 3e-3), ("f16", 5e-4)])
+def test_batched_matches_oracle(dtype, tol):
+    probs = _problems()
+    geoms = [p[1] for p in probs]
+    g_list = [p[2] for p in probs]
+    rng = np.random.default_rng(17)
+    W_np = [rng.uniform(0.2, 0.8, size=(gm.V,) + gm.sino_shape).astype(np.float32)
+            for gm in geoms]
+    W_list = [torch.as_tensor(Wn, device="cuda") for Wn in W_np]
+    # one problem keeps the default weight 1/2
+    W_list[1] = None
+    batch = api.Batch(geoms, dtype=dtype, kahan=(dtype != "f32"))
+    vols = [torch.full(geom.vol_shape, float("nan"), device="cuda") for geom in geoms]
+    batch.run(g_list, vols, W_list)
+    torch.cuda.synchronize()
+    errs = []
+    for i, ((w, geom, g), v) in enumerate(zip(probs, vols)):
+        og = orc.Geometry(w.desc_dict(), w.matrices(), w.orbit.vdl)
+        g_np = g.double().cpu().numpy()[None]
+        ref = orc.reconstruct(og, g_np, None if W_list[i] is None else W_np[i])[0]
+        errs.append(rel_l2(v.double().cpu().numpy(), ref))
+    assert max(errs) < tol, errs
+    for geom in geoms:
+        api.dc_sync_status(geom)
+    batch.close()
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import oracle as orc
 from paper_2410_14900_gb300 import _lib as L
 from paper_2410_14900_gb300 import api, synth
 
@@ -50,6 +51,11 @@ def test_noalloc_matches_handle_entry_point_twice(V, H, W, p, n_mu, n_s, ds):
         want = ref[0].double().cpu().numpy()
         assert np.isfinite(got).all()
         assert rel_l2(got, want) < 2e-6
+        # and directly against the FP64 oracle's Joseph line sums (Eq. 7)
+        img_h = img[0].double().cpu().numpy()
+        for i in range(V):
+            ref_o = orc.radon(img_h[i], p, n_mu, n_s, ds, cu, cv)
+            assert rel_l2(got[i], ref_o) < 2e-6
 
 
 def test_noalloc_rejects_sizes_beyond_its_maximum():
@@ -60,6 +66,13 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
     rc = Lh.dc_radon2d_noalloc(1, 4096, 4096, 90, 4096, 1.0, 1.0, 2047.5, 2047.5, ptr, ptr, None)
     assert rc == L.DC_ERR_ARG
     assert b"fixed" in Lh.dc_last_error()
+    # the limit is H * round4(W) * 4 bytes <= 32 MiB - 256 KiB: 2000 rows of
+    # 4096 floats (31.25 MiB) are beyond it, 1984 rows (31.0 MiB) within it
+    rc = Lh.dc_radon2d_noalloc(1, 2000, 4096, 90, 64, 1.0, 1.0, 2047.5, 999.5, ptr, ptr, None)
+    assert rc == L.DC_ERR_ARG
+    assert b"fixed" in Lh.dc_last_error()
+    cap = (32 << 20) - (256 << 10)
+    assert 1984 * 4096 * 4 <= cap < 2000 * 4096 * 4
     rc = Lh.dc_radon2d_noalloc(1, 64, 64, 4096, 64, 1.0, 1.0, 31.5, 31.5, ptr, ptr, None)
     assert rc == L.DC_ERR_ARG
     rc = Lh.dc_radon2d_noalloc(1, 64, 64, 90, 64, 1.0, 1.0, 31.5, 31.5, None, ptr, None)
