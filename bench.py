@@ -310,6 +310,68 @@ def train_step_measure(args, dev, L, world):
             "note": "forward + backward + optimizer step"}
 
 
+def train_step_512_measure(args, dev, L):
+    """Forward + backward + AdamW step at the 512^3 circle-plus-arc geometry
+    (496 views, 384x512 detector, W of 496 x 720 x 512), batch 1, Gaussian
+    filter layer on W, MSE against the phantom volume, ReLU output; once
+    with Grangeat's S kept between the passes and once with S recomputed
+    per chunk of 32 views (only g kept).  Reports each step's time and the
+    peak of torch's allocator (every tensor of the step: projections,
+    volumes, W with its gradient and AdamW moments, the kept S) plus the
+    library's own work area."""
+    import torch
+    from paper_2410_14900_gb300 import api, synth
+    from paper_2410_14900_gb300.autograd import DefriseClackNet
+
+    w = synth.workload("circle_arc512")
+    geom = api.Geometry(w.desc_dict(), w.matrices(), w.orbit.vdl)
+    blobs = w.phantoms()[0]
+    g = synth.project_phantom(blobs, w.orbit, w.det_rows, w.det_cols, w.pitch,
+                              device=dev, dtype=torch.float32)[None].contiguous()
+    tgt = synth.phantom_volume(blobs, w.vol_shape, w.voxel, device=dev)[None]
+    t = api.dc_geometry_get_tuning(geom)
+    per_img = 4 * (w.det_rows * ((w.det_cols + 3) // 4 * 4)
+                   + 2 * w.n_mu * ((w.n_s + 3) // 4 * 4))
+    work_bytes = int(t["chunk_capacity"]) * per_img
+    stream = torch.cuda.current_stream()
+    out = {"workload": w.name, "batch": 1, "views": w.n_views, "volume": list(w.vol_shape),
+           "weights": [w.n_views, w.n_mu, w.n_s], "optimizer": "AdamW (lr 1e-3)",
+           "smooth": [20.0, 60], "library_work_area_bytes": work_bytes,
+           "note": "forward + backward + optimizer step"}
+    steps = max(1, min(args.steps, 3))
+    for name, cache_s, chunk in (("kept_s", True, 0), ("recompute_s_chunk32", False, 32)):
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        torch.cuda.reset_peak_memory_stats(dev)
+        net = DefriseClackNet(geom, init=0.5, relu=True, device=dev, smooth=(20.0, 60),
+                              cache_s=cache_s, view_chunk=chunk)
+        opt = torch.optim.AdamW(net.parameters(), lr=1e-3)
+
+        def step():
+            opt.zero_grad(set_to_none=True)
+            loss = torch.nn.functional.mse_loss(net(g), tgt)
+            loss.backward()
+            opt.step()
+            return loss
+
+        step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            loss = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_step": e0.elapsed_time(e1) / steps, "steps": steps,
+                     "torch_peak_bytes": int(torch.cuda.max_memory_allocated(dev)),
+                     "view_chunk": chunk, "loss": float(loss.item())}
+        del net, opt
+    api.dc_sync_status(geom)
+    geom.close()
+    return out
+
+
 # --------------------------------------------------------------- batched
 def batched_measure(args, dev, L):
     """12 uneven orbits (4 circular, 4 sinusoidal, 4 circle plus arc; 200-720
@@ -606,10 +668,12 @@ def run_ours(args, rank, world, local_rank):
         paper_shape = paper_shape_measure(args, dev, L)
 
     train = None
+    train512 = None
     if not args.no_train:
         del gF, vol
         torch.cuda.empty_cache()
         train = train_step_measure(args, dev, L, world)
+        train512 = train_step_512_measure(args, dev, L)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -629,6 +693,7 @@ def run_ours(args, rank, world, local_rank):
                                tuning={k: tuned[k] for k in ("chunk_images", "bp_nz")},
                                l2="inputs larger than L2 (g 390 MB, f 537 MB), no flush"),
                 "roofline": roof, "breakdown": breakdown, "forms": forms, "train_step": train,
+                "train_step_512": train512,
                 "batched": batched, "paper_shape": paper_shape,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(n_launch),
                 "clocks": clocks}
@@ -655,8 +720,10 @@ def main():
         import torch
         from paper_2410_14900_gb300 import _lib
         torch.cuda.set_device(local_rank)
-        print(json.dumps({"train_step": train_step_measure(args, torch.device("cuda", local_rank),
-                                                           _lib.load(), world)}), flush=True)
+        dev = torch.device("cuda", local_rank)
+        print(json.dumps({"train_step": train_step_measure(args, dev, _lib.load(), world),
+                          "train_step_512": train_step_512_measure(args, dev, _lib.load())}),
+              flush=True)
         return
     if world > 1:
         import torch

@@ -310,9 +310,14 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
   const size_t np = (size_t)a.H * a.W;
   const T *gbase = (const T *)a.gF + (size_t)b * a.V * np;
 
-  float acc[NZ], cmp[NZ];
+  // With KAHAN each view chunk's terms are summed in plain FP32 into prt[],
+  // and the chunk sums are added to acc[] with Kahan compensation (cmp[]),
+  // so the compensated sum runs over the V / TB_VCH chunk sums rather than
+  // every view: the FP32 error is that of a TB_VCH-term sum, at 1/TB_VCH of
+  // the per-view compensation cost.  Without KAHAN terms go to acc[].
+  float acc[NZ], cmp[NZ], prt[NZ];
 #pragma unroll
-  for (int k = 0; k < NZ; ++k) acc[k] = cmp[k] = 0.0f;
+  for (int k = 0; k < NZ; ++k) acc[k] = cmp[k] = prt[k] = 0.0f;
 
   bool ok = true;
   for (int c0 = 0; c0 < a.V && ok; c0 += TB_VCH) {
@@ -465,14 +470,8 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
               float val = fmaf(fv, x1 - x0, x0);
               float ez = fmaf(kf, a.dz, ez0);
               float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
-              if (KAHAN) {
-                float y = term - cmp[k];
-                float tt = acc[k] + y;
-                cmp[k] = (tt - acc[k]) - y;
-                acc[k] = tt;
-              } else {
-                acc[k] += term;
-              }
+              if (KAHAN) prt[k] += term;
+              else acc[k] += term;
             }
           } else {
 #pragma unroll
@@ -486,14 +485,8 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
               float val = fmaf(fv, x1 - x0, x0);
               float ez = fmaf(kf, a.dz, ez0);
               float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
-              if (KAHAN) {
-                float y = term - cmp[k];
-                float tt = acc[k] + y;
-                cmp[k] = (tt - acc[k]) - y;
-                acc[k] = tt;
-              } else {
-                acc[k] += term;
-              }
+              if (KAHAN) prt[k] += term;
+              else acc[k] += term;
             }
           }
         } else {
@@ -521,14 +514,8 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
               float val = fmaf(fv, x1 - x0, x0);
               float ez = fmaf(kf, a.dz, ez0);
               float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
-              if (KAHAN) {
-                float y = term - cmp[k];
-                float tt = acc[k] + y;
-                cmp[k] = (tt - acc[k]) - y;
-                acc[k] = tt;
-              } else {
-                acc[k] += term;
-              }
+              if (KAHAN) prt[k] += term;
+              else acc[k] += term;
             }
           } else {
 #pragma unroll
@@ -546,14 +533,8 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
               float val = fmaf(fv, x1 - x0, x0);
               float ez = fmaf(kf, a.dz, ez0);
               float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
-              if (KAHAN) {
-                float y = term - cmp[k];
-                float tt = acc[k] + y;
-                cmp[k] = (tt - acc[k]) - y;
-                acc[k] = tt;
-              } else {
-                acc[k] += term;
-              }
+              if (KAHAN) prt[k] += term;
+              else acc[k] += term;
             }
           }
         }
@@ -570,15 +551,19 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
           float val = bilinear<T>(img, a.H, a.W, u, v) * sc;
           float ez = fmaf(kf, a.dz, ez0);
           float term = val * __frcp_rn(fmaf(ez, ez, rho2));
-          if (KAHAN) {
-            float y = term - cmp[k];
-            float tt = acc[k] + y;
-            cmp[k] = (tt - acc[k]) - y;
-            acc[k] = tt;
-          } else {
-            acc[k] += term;
-          }
+          if (KAHAN) prt[k] += term;
+          else acc[k] += term;
         }
+      }
+    }
+    if (KAHAN && ok) {
+#pragma unroll
+      for (int k = 0; k < NZ; ++k) {
+        const float y = prt[k] - cmp[k];
+        const float tt = acc[k] + y;
+        cmp[k] = (tt - acc[k]) - y;
+        acc[k] = tt;
+        prt[k] = 0.0f;
       }
     }
   }

@@ -56,8 +56,13 @@ def wide_footprint_case():
     return _case(o, 96, 128, 0.25, 40, 128, (32, 24, 24), (2.0, 2.0, 2.0), name="wide")
 
 
-@pytest.mark.parametrize("make", [behind_source_case, wide_footprint_case])
-def test_backprojection_global_paths_match_oracle(make):
+# FP32 floor of the detector position with white-noise data (neighbouring
+# pixels uncorrelated, so a position error of e pixels is a relative value
+# error of about e): voxels 1.4 mm from the source are magnified ~45x, and
+# 0.25 mm pixels put 4800 pixels per unit of lateral slope, so FP32 rounding
+# of the coordinates moves projections by 1e-5 to 1e-4 pixel
+@pytest.mark.parametrize("make,tol", [(behind_source_case, 5e-5), (wide_footprint_case, 5e-5)])
+def test_backprojection_global_paths_match_oracle(make, tol):
     case = make()
     d = case.desc
     gg = api.Geometry(d, case.P, case.vdl)
@@ -68,12 +73,12 @@ def test_backprojection_global_paths_match_oracle(make):
     assert np.abs(ref).max() > 0
     for kahan in (False, True):
         vol = _host(api.dc_backproject(gg, _dev(gF), kahan=kahan))
-        assert rel_l2(vol, ref) < 1e-5
+        assert rel_l2(vol, ref) < tol
     # the transpose through the same paths
     gv = rng.normal(size=(case.B, d["vol_z"], d["vol_y"], d["vol_x"])).astype(np.float32)
     adj = _host(api.dc_backproject_adjoint(gg, _dev(gv)))
     ref_adj = orc.backproject_adjoint(og, gv)
-    assert rel_l2(adj, ref_adj) < 1e-5
+    assert rel_l2(adj, ref_adj) < tol
     api.dc_sync_status(gg)
 
 
@@ -95,7 +100,7 @@ def test_behind_source_voxels_get_nothing_from_those_views():
     behind = depth <= 0
     assert behind.any() and (~behind).any()
     assert np.all(vol[behind] == 0.0) and np.all(ref[behind] == 0.0)
-    assert rel_l2(vol, ref) < 1e-5
+    assert rel_l2(vol, ref) < 5e-5
 
 
 def test_full_reconstruction_behind_source_matches_oracle():

@@ -66,13 +66,13 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
     rc = Lh.dc_radon2d_noalloc(1, 4096, 4096, 90, 4096, 1.0, 1.0, 2047.5, 2047.5, ptr, ptr, None)
     assert rc == L.DC_ERR_ARG
     assert b"fixed" in Lh.dc_last_error()
-    # the limit is H * round4(W) * 4 bytes <= 32 MiB - 256 KiB: 2000 rows of
-    # 4096 floats (31.25 MiB) are beyond it, 1984 rows (31.0 MiB) within it
-    rc = Lh.dc_radon2d_noalloc(1, 2000, 4096, 90, 64, 1.0, 1.0, 2047.5, 999.5, ptr, ptr, None)
+    # the limit is H * round4(W) * 4 bytes <= 32 MiB - 256 KiB: 2040 rows of
+    # 4096 floats are beyond it (2032 rows fill it exactly)
+    rc = Lh.dc_radon2d_noalloc(1, 2040, 4096, 90, 64, 1.0, 1.0, 2047.5, 1019.5, ptr, ptr, None)
     assert rc == L.DC_ERR_ARG
     assert b"fixed" in Lh.dc_last_error()
     cap = (32 << 20) - (256 << 10)
-    assert 1984 * 4096 * 4 <= cap < 2000 * 4096 * 4
+    assert 2032 * 4096 * 4 == cap < 2040 * 4096 * 4
     rc = Lh.dc_radon2d_noalloc(1, 64, 64, 4096, 64, 1.0, 1.0, 31.5, 31.5, ptr, ptr, None)
     assert rc == L.DC_ERR_ARG
     rc = Lh.dc_radon2d_noalloc(1, 64, 64, 90, 64, 1.0, 1.0, 31.5, 31.5, None, ptr, None)
