@@ -31,6 +31,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "512³ DC-FBP recon ms/volume"
+# bounded sample of the oracle at the 512^3 workload: 32 views of the filter
+# and 20000 voxels of the backprojection over all views
+ORACLE_SAMPLE_VIEWS = 32
+ORACLE_SAMPLE_VOXELS = 20000
 UNIT = "ms/volume"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -210,7 +214,31 @@ def oracle_sample(w, g_np, n_views_sample: int, n_vox_sample: int, seed: int = 0
     ms = 1e3 * (t_f * V / len(views) + t_b * nvox / len(flat))
     sample = (f"FP64 oracle filter on {len(views)} of {V} views and backprojection of "
               f"{len(flat)} of {nvox} voxels over all views, scaled linearly to one volume")
-    return ms, sample, orc.num_threads(), t_f + t_b
+    return ms, sample, orc.num_threads(), t_f + t_b, len(views), len(flat)
+
+
+def oracle_full(names=("circle64", "sinusoid256"), device=None) -> dict:
+    """The FP64 oracle's complete reconstruction (Eq. 12, no sampling) of the
+    two smaller configurations: 64-view circle 64^2 -> 64^3 and 360-view
+    sinusoid 256^2 -> 256^3, timed on the host cores (the input projections
+    are generated beforehand, on `device` if given, outside the timing)."""
+    import torch
+    from oracle import oracle as orc
+    from paper_2410_14900_gb300 import synth
+    out = {}
+    for name in names:
+        w = synth.workload(name)
+        og = orc.Geometry(w.desc_dict(), w.matrices(), w.orbit.vdl)
+        g = synth.project_phantom(w.phantoms()[0], w.orbit, w.det_rows, w.det_cols, w.pitch,
+                                  device=device, dtype=torch.float64)
+        if device is not None:
+            g = g.cpu().numpy()
+        t0 = time.perf_counter()
+        orc.reconstruct(og, g[None])
+        out[name] = {"ms_per_volume": 1e3 * (time.perf_counter() - t0), "views": w.n_views,
+                     "detector": [w.det_rows, w.det_cols], "volume": list(w.vol_shape),
+                     "extrapolated": False}
+    return out
 
 
 def workload_config(w, storage: str, B: int, world: int) -> dict:
@@ -232,24 +260,25 @@ def run_reference(args, rank, world):
     # a small stand-in projection set is enough: the oracle's cost does not
     # depend on the values
     g = np.random.default_rng(0).standard_normal((w.n_views, w.det_rows, w.det_cols))
-    from oracle import oracle as orc
-    cores = orc.num_threads()
-    nv = max(1, min(cores, w.n_views))
-    nvox = 20000
+    nv = min(ORACLE_SAMPLE_VIEWS, w.n_views)
+    nvox = ORACLE_SAMPLE_VOXELS
     for _ in range(args.warmup):
         oracle_sample(w, g, 1, 1000)
     times = []
     sample = ""
+    cores = 0
     for k in range(args.steps):
-        ms, sample, cores, _ = oracle_sample(w, g, nv, nvox, seed=k)
+        ms, sample, cores, _, nvs, nxs = oracle_sample(w, g, nv, nvox, seed=k)
         times.append(ms)
     val = statistics.mean(times)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": val,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(w, args.storage, 1, world),
+            "extrapolated": True,
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "extrapolated": True, "sample_views": nvs,
+                             "sample_voxels": nxs, "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -339,10 +368,10 @@ def train_step_512_measure(args, dev, L):
            "smooth": [20.0, 60], "library_work_area_bytes": work_bytes,
            "note": "forward + backward + optimizer step"}
     steps = max(1, min(args.steps, 3))
-    for name, cache_s, chunk in (("kept_s", True, 0), ("recompute_s_chunk32", False, 32)):
-        torch.cuda.synchronize()
-        torch.cuda.empty_cache()
-        torch.cuda.reset_peak_memory_stats(dev)
+
+    def measure(cache_s, chunk):
+        # everything of one setting (the net, AdamW's moments, the autograd
+        # graph of the last loss) dies when this returns
         net = DefriseClackNet(geom, init=0.5, relu=True, device=dev, smooth=(20.0, 60),
                               cache_s=cache_s, view_chunk=chunk)
         opt = torch.optim.AdamW(net.parameters(), lr=1e-3)
@@ -352,7 +381,7 @@ def train_step_512_measure(args, dev, L):
             loss = torch.nn.functional.mse_loss(net(g), tgt)
             loss.backward()
             opt.step()
-            return loss
+            return loss.detach()
 
         step()
         torch.cuda.synchronize()
@@ -363,10 +392,17 @@ def train_step_512_measure(args, dev, L):
             loss = step()
         e1.record(stream)
         torch.cuda.synchronize()
-        out[name] = {"ms_per_step": e0.elapsed_time(e1) / steps, "steps": steps,
-                     "torch_peak_bytes": int(torch.cuda.max_memory_allocated(dev)),
-                     "view_chunk": chunk, "loss": float(loss.item())}
-        del net, opt
+        return {"ms_per_step": e0.elapsed_time(e1) / steps, "steps": steps,
+                "torch_peak_bytes": int(torch.cuda.max_memory_allocated(dev)),
+                "view_chunk": chunk, "loss": float(loss)}
+
+    import gc
+    for name, cache_s, chunk in (("kept_s", True, 0), ("recompute_s_chunk32", False, 32)):
+        gc.collect()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        torch.cuda.reset_peak_memory_stats(dev)
+        out[name] = measure(cache_s, chunk)
     api.dc_sync_status(geom)
     geom.close()
     return out
@@ -678,10 +714,11 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g_np = g[0].double().cpu().numpy()
-        from oracle import oracle as orc
-        nv = max(1, min(orc.num_threads(), V))
-        ms, sample, cores, _ = oracle_sample(w, g_np, nv, 20000)
-        cpu = {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        nv = min(ORACLE_SAMPLE_VIEWS, V)
+        ms, sample, cores, _, nvs, nxs = oracle_sample(w, g_np, nv, ORACLE_SAMPLE_VOXELS)
+        cpu = {"value": ms, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "extrapolated": True, "sample_views": nvs, "sample_voxels": nxs,
+               "sample": sample, "full_runs": oracle_full(device=dev)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": sharding.whole_job_ms_per_volume(ms_step, B, world),
@@ -689,9 +726,9 @@ def run_ours(args, rank, world, local_rank):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic: seeded 20-ellipsoid phantom, exact line integrals",
-                "config": dict(workload_config(w, args.storage, B, world),
-                               tuning={k: tuned[k] for k in ("chunk_images", "bp_nz")},
-                               l2="inputs larger than L2 (g 390 MB, f 537 MB), no flush"),
+                "config": workload_config(w, args.storage, B, world),
+                "tuning": {k: tuned[k] for k in ("chunk_images", "bp_nz")},
+                "l2": "inputs larger than L2 (g 390 MB, f 537 MB), no flush",
                 "roofline": roof, "breakdown": breakdown, "forms": forms, "train_step": train,
                 "train_step_512": train512,
                 "batched": batched, "paper_shape": paper_shape,
