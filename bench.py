@@ -672,7 +672,7 @@ def run_ours(args, rank, world, local_rank):
     # the chosen low-precision form next to the plain FP32 path
     forms = None
     if not args.no_forms and args.storage == "f32":
-        forms = {}
+        forms = {"f32_gF_bytes_per_volume": int(gF.numel() * gF.element_size())}
         for st in ("bf16", "f16"):
             # voxels per thread along z tuned for this storage form with Kahan
             ft = tune.autotune(geom, st, chunks=(tuned["chunk_images"],), nzs=(16, 32), kahan=True)
@@ -693,6 +693,8 @@ def run_ours(args, rank, world, local_rank):
             f1.record(stream)
             torch.cuda.synchronize()
             forms[f"{st}_storage_kahan_ms_per_volume"] = f0.elapsed_time(f1) / args.steps
+            forms[f"{st}_gF_bytes_per_volume"] = int(gF2.numel() * gF2.element_size()
+                                                     + (sc2.numel() * 4 if sc2 is not None else 0))
             del gF2
 
     batched = None

@@ -18,6 +18,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "dc_async.cuh"
@@ -416,17 +417,34 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
           }
         } else {
           // 16-bit storage: four values per 8-byte load, converted (and
-          // scaled) to FP32 pairs with two 16-byte stores
+          // scaled) to FP32 pairs with two 16-byte stores.  A BF16 value is
+          // the upper half of the FP32 with the same bits, so its conversion
+          // is a shift or a mask (exact), and BF16 storage has no scale.
+          constexpr bool BF = std::is_same<T, __nv_bfloat16>::value;
           const int lg = (bw == TB_BWN) ? 3 : 4;
           for (int e = tid; e < (TB_BH * bw) >> 2; e += TB_TX * TB_TY) {
             int r = e >> lg, j4 = (e - (r << lg)) << 2;
             const T *src = raw + r * bw + j4;
             uint2 pk = *(const uint2 *)src;
-            T h[4];
-            memcpy(h, &pk, sizeof(pk));
-            float v0 = sld(&h[0]) * sc, v1 = sld(&h[1]) * sc, v2 = sld(&h[2]) * sc,
-                  v3 = sld(&h[3]) * sc;
-            float nx = (j4 + 4 < bw) ? sld(src + 4) * sc : 0.0f;
+            float v0, v1, v2, v3, nx;
+            if (BF) {
+              v0 = __uint_as_float(pk.x << 16);
+              v1 = __uint_as_float(pk.x & 0xffff0000u);
+              v2 = __uint_as_float(pk.y << 16);
+              v3 = __uint_as_float(pk.y & 0xffff0000u);
+              nx = (j4 + 4 < bw)
+                       ? __uint_as_float((unsigned)*reinterpret_cast<const unsigned short *>(src + 4)
+                                         << 16)
+                       : 0.0f;
+            } else {
+              T h[4];
+              memcpy(h, &pk, sizeof(pk));
+              v0 = sld(&h[0]) * sc;
+              v1 = sld(&h[1]) * sc;
+              v2 = sld(&h[2]) * sc;
+              v3 = sld(&h[3]) * sc;
+              nx = (j4 + 4 < bw) ? sld(src + 4) * sc : 0.0f;
+            }
             float4 *dst = (float4 *)(wt + r * TB_S2 + j4);
             dst[0] = make_float4(v0, v1 - v0, v1, v2 - v1);
             dst[1] = make_float4(v2, v3 - v2, v3, nx - v3);
@@ -1114,8 +1132,9 @@ int dc_backproject_adjoint(const dc_geometry *g, int B, const float *grad_vol,
 }  // extern "C"
 
 // ------------------------------------------------------------------------
-// Batched reconstruction: per-problem filters, then one persistent
-// backprojection over all problems.  Everything a run needs is allocated by
+// Batched reconstruction: one persistent filter kernel over the (problem,
+// view) images of all problems, then one persistent backprojection over all
+// problems' voxel boxes.  Everything a run needs is allocated by
 // dc_batch_create, so dc_batch_run allocates nothing and can be captured in
 // a CUDA graph.
 struct dc_batch {
@@ -1132,6 +1151,7 @@ struct dc_batch {
   BatchProblem *d_probs;
   CUtensorMap *d_maps;
   unsigned long long *d_counter;
+  dc::BatchFilterPlan *fplan;     // persistent filter of every problem (NULL: per-problem calls)
 };
 
 namespace {
@@ -1145,6 +1165,7 @@ void free_batch(dc_batch *b) {
   cudaFree(b->d_probs);
   cudaFree(b->d_maps);
   cudaFree(b->d_counter);
+  dc::batch_filter_destroy(b->fplan);
   delete b;
 }
 
@@ -1271,6 +1292,14 @@ int dc_batch_create(int n, dc_geometry *const *geoms, int dtype, unsigned flags,
   if (e != cudaSuccess) return bail(dc::cuda_fail(e, "dc_batch_create: tables"));
   int rc = build_batch_tables(b);
   if (rc) return bail(rc);
+  // one persistent launch filters every problem; problems whose rows do not
+  // fit its shared memory keep the per-problem filter calls
+  rc = dc::batch_filter_create(n, b->geoms, dtype, b->gF, b->scale, &b->fplan);
+  if (rc == DC_ERR_UNSUPPORTED) {
+    b->fplan = nullptr;
+  } else if (rc) {
+    return bail(rc);
+  }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   b->grid = std::max(1, sms) * 2;
@@ -1292,10 +1321,15 @@ int dc_batch_run(dc_batch *b, const float *const *g, const float *const *W, floa
   for (int i = 0; i < b->n; ++i)
     if (!g[i] || !vol[i]) return dc::fail(DC_ERR_ARG, "dc_batch_run: NULL g or vol");
   cudaStream_t st = (cudaStream_t)stream;
-  for (int i = 0; i < b->n; ++i) {
-    int rc = dc_filter(b->geoms[i], 1, g[i], W ? W[i] : nullptr, b->gF[i], b->dtype,
-                       b->scale[i], stream);
+  if (b->fplan) {
+    int rc = dc::batch_filter_run(b->fplan, g, W, st);
     if (rc) return rc;
+  } else {
+    for (int i = 0; i < b->n; ++i) {
+      int rc = dc_filter(b->geoms[i], 1, g[i], W ? W[i] : nullptr, b->gF[i], b->dtype,
+                         b->scale[i], stream);
+      if (rc) return rc;
+    }
   }
   BatchRun run;
   memset(&run, 0, sizeof(run));

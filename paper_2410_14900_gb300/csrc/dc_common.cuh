@@ -50,6 +50,7 @@ enum KernelId {
   KID_BP3D_ADJ,
   KID_SMOOTH,
   KID_ADJ_S,
+  KID_FILTER_BATCHED,
   KID_COUNT
 };
 
@@ -185,6 +186,14 @@ int backproject_check(const dc_geometry *g, int B, const void *gF, int dtype,
 int backproject_slab(const dc_geometry *g, int B, const void *gF, int dtype,
                      const float *gF_scale, float *vol, unsigned flags, int z_begin, int z_end,
                      cudaStream_t st, bool *used);
+// the batched persistent filter (dc_filter.cu): one launch filters every
+// view of up to 32 problems into the given g^F buffers (and FP16 scales)
+struct BatchFilterPlan;
+int batch_filter_create(int n, dc_geometry *const *geoms, int dtype, void *const *gF,
+                        float *const *scale, BatchFilterPlan **out);
+int batch_filter_run(BatchFilterPlan *p, const float *const *g, const float *const *W,
+                     cudaStream_t st);
+void batch_filter_destroy(BatchFilterPlan *p);
 // FP64 split of v into hi (12 fractional bits) + lo
 inline __host__ __device__ float split_hi12(double v) {
   return (float)(rint(v * 4096.0) / 4096.0);

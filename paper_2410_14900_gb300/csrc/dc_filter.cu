@@ -30,6 +30,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "dc_async.cuh"
 #include "dc_common.cuh"
@@ -81,14 +82,12 @@ __global__ void __launch_bounds__(256) k_prep(PrepArgs a) {
 enum { M_RAW = 0, M_GRANGEAT = 1, M_FILTER = 2, M_DIFFSTORE = 3, M_ADJ = 4 };
 
 constexpr int LS_THREADS = 640;  // one CTA per SM: 20 warps at 96 registers
-constexpr int LS_WARPS = LS_THREADS / 32;
 // A band of RB detector rows (32, or 16 / 8 when long detector rows would
 // not fit) is staged with RB + 1 floats per sample: odd, so lanes at distinct
 // samples hit distinct banks.  RB + 1 zero samples pad each side: a line that
 // meets the detector anywhere in a band moves less than RB samples (slope at
 // most 1) over the band, so its taps never leave the stage and need no clamp.
 constexpr int LS_SMEM_BUDGET = 225 * 1024;  // one CTA per SM
-static_assert(LS_WARPS <= dc::DC_LS_MAX_TASKS, "task table size");
 
 struct LineArgs {
   const float *img;   // [n][H][Wp]
@@ -161,18 +160,22 @@ __device__ __forceinline__ float band_sum(const char *sb, unsigned cb, int nr, f
   return sum;
 }
 
-template <int MODE, int RB>
-__global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
+// The line sums of angle group `gi` of image n (view a.v0 + n / a.B, item
+// a.b0 + n % a.B) by a CTA of NT threads (a 1-D block).  The image is read
+// from work-area slot `slot` of a.img and the scratch sinograms are written
+// to slot `slot` of a.out / a.sinoA / a.sinoB (the chunked launches use
+// slot = n).  Uses `smem` (dynamic, linesum_smem_for bytes), lmu and ttab;
+// the CTA must synchronise before calling it again.
+template <int MODE, int RB, int NT>
+__device__ __forceinline__ void linesum_body(const LineArgs &a, int gi, int n, int slot,
+                                             float *smem, LineMu *lmu, short2 *ttab) {
   constexpr bool DIFF = (MODE != M_RAW);
   constexpr int LS_RB = RB, LS_SQ = RB + 1, LS_PJ = RB + 1;
+  constexpr int LS_THREADS = NT, LS_WARPS = NT / 32;
   static_assert(LS_THREADS % RB == 0 && RB <= 32, "band copy mapping");
-  constexpr int STRIDE_L = DIFF ? 31 : 32;  // lines per task (diff: one overlap)
-  extern __shared__ __align__(16) float smem[];
-  __shared__ LineMu lmu[dc::DC_LS_MAX_MG];
-  __shared__ short2 ttab[dc::DC_LS_MAX_TASKS];
+    constexpr int STRIDE_L = DIFF ? 31 : 32;  // lines per task (diff: one overlap)
 
-  const int n = blockIdx.y;
-  const dc::MuGroup G = a.groups[blockIdx.x];
+  const dc::MuGroup G = a.groups[gi];
   const int v = a.v0 + n / a.B, b = a.b0 + n % a.B;
   const dc::FView fv = a.fv[v];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
   // the fastest index, so inside the unrolled band loop it is an immediate.
   const int rows = G.branch ? a.W : a.H;  // steps along a line
   const int len = G.branch ? a.H : a.W;   // samples across a line
-  const float *src = a.img + (size_t)n * a.H * a.Wp;
+  const float *src = a.img + (size_t)slot * a.H * a.Wp;
   const int stage_sz = (len + 2 * LS_PJ) * LS_SQ;
   float *stage0 = smem;
   float *stage1 = smem + stage_sz;
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
     for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
       int ml = idx / a.NSp, k = idx % a.NSp;
       int m = a.mu_order[G.first + ml];
-      a.sinoA[((size_t)n * a.n_mu + m) * a.NSp + k] = (k <= a.n_s - 2) ? ep[idx] : 0.0f;
+      a.sinoA[((size_t)slot * a.n_mu + m) * a.NSp + k] = (k <= a.n_s - 2) ? ep[idx] : 0.0f;
     }
     return;
   }
@@ -362,7 +365,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
         float qm = (k > 0) ? ep[idx - 1] : 0.0f;
         val = (ep[idx] - qm) / a.ds * a.cT * lmu[ml].jscale;
       }
-      a.out[((size_t)n * a.n_mu + m) * a.NSp + k] = val;
+      a.out[((size_t)slot * a.n_mu + m) * a.NSp + k] = val;
     }
     return;
   }
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
     for (int idx = threadIdx.x; idx < total; idx += LS_THREADS) {
       int ml = idx / a.NSp, k = idx % a.NSp;
       int m = a.mu_order[G.first + ml];
-      size_t o = ((size_t)n * a.n_mu + m) * a.NSp + k;
+      size_t o = ((size_t)slot * a.n_mu + m) * a.NSp + k;
       float y = 0.0f, tW = 0.0f;
       if (k <= a.n_s - 2) {
         float sh = s_half(k);
@@ -401,9 +404,17 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
         float y0 = (k <= a.n_s - 2) ? ep[idx] : 0.0f;
         val = (ym - y0) / a.ds * lmu[ml].jscale;
       }
-      a.sinoB[((size_t)n * a.n_mu + m) * a.NSp + k] = val;
+      a.sinoB[((size_t)slot * a.n_mu + m) * a.NSp + k] = val;
     }
   }
+}
+
+template <int MODE, int RB>
+__global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ LineMu lmu[dc::DC_LS_MAX_MG];
+  __shared__ short2 ttab[dc::DC_LS_MAX_TASKS];
+  linesum_body<MODE, RB, LS_THREADS>(a, blockIdx.x, blockIdx.y, blockIdx.y, smem, lmu, ttab);
 }
 
 // ----------------------------------------------------- 2-D backprojection
@@ -444,48 +455,73 @@ struct BPMu {
   int pad1, pad2;
 };
 
+// Barrier of one group of BP2_THREADS threads (named barrier `id`; id 0 with
+// a CTA of exactly BP2_THREADS threads is __syncthreads), and its OR-reduction.
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(BP2_THREADS) : "memory");
+}
+__device__ __forceinline__ bool group_sync_or(int id, bool pred) {
+  unsigned r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((unsigned)pred), "r"(id), "n"(BP2_THREADS)
+      : "memory");
+  return r != 0;
+}
+
+// One BP2_TX x (8 RY) pixel tile (tile_x, tile_y) of image n (view
+// a.v0 + n / a.B, item a.b0 + n % a.B) by a group of BP2_THREADS threads (gt:
+// thread within the group; barrier `bar_id`).  The sinograms come from
+// work-area slot `slot` of a.sino; OUT_F32_ABSMAX writes slot `slot` of the
+// scratch and a.absmax[slot].  `smem` holds the group's two stages, `bars`
+// its two mbarriers (initialised by the caller), `bmu` its per-angle
+// constants; `it` counts the angle chunks the group has staged so far (the
+// stage and the barrier phase of the next chunk follow from it).  Returns
+// false if a bounded wait gave up.
+//
 // MULTI: ds < pitch, where the transposed Joseph hat of an angle (half-width
 // 1/winv s-bins, at most 3 for ds >= pitch/3) covers up to six taps; those
 // are summed with explicit bounds instead of the two-tap fast paths.
-template <bool MULTI>
-__global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
-  extern __shared__ __align__(16) float smem[];
-  __shared__ uint64_t bars[2];
-  __shared__ BPMu bmu[2][BP2_MC];
-  const int n = blockIdx.z;
+template <bool MULTI, int RY>
+__device__ __forceinline__ bool bp2d_tile(const BP2Args &a, int n, int slot, int tile_x,
+                                          int tile_y, int gt, int bar_id, float *smem,
+                                          uint64_t *bars, BPMu (*bmu)[BP2_MC], unsigned &it) {
   const int v = a.v0 + n / a.B, b = a.b0 + n % a.B;
   const dc::FView fv = a.fv[v];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j0 = blockIdx.x * BP2_TX, r0 = blockIdx.y * BP2_TY;
+  const int warp = gt >> 5, lane = gt & 31;
+  constexpr int TY = 8 * RY;  // tile rows: RY per warp
+  const int j0 = tile_x * BP2_TX, r0 = tile_y * TY;
   const int rstride = a.NSp + PADL + PADR;
   const int stage_sz = BP2_MC * rstride;
-  const float *src = a.sino + (size_t)n * a.n_mu * a.NSp;
+  const float *src = a.sino + (size_t)slot * a.n_mu * a.NSp;
   const int nchunk = (a.n_mu + BP2_MC - 1) / BP2_MC;
   const char *sb = reinterpret_cast<const char *>(smem);
+  const unsigned it0 = it;
 
-  if (threadIdx.x == 0) {
-    dc::mbar_init(&bars[0], 1);
-    dc::mbar_init(&bars[1], 1);
-    dc::fence_barrier_init();
-  }
-  for (int i = threadIdx.x; i < 2 * BP2_MC; i += BP2_THREADS) {
+  // zero pads left and right of every stage row (the copies fill the middle)
+  for (int i = gt; i < 2 * BP2_MC; i += BP2_THREADS) {
     float *row = smem + (size_t)i * rstride;
     for (int t = 0; t < PADL; ++t) row[t] = 0.0f;
     for (int t = PADL + a.NSp; t < rstride; ++t) row[t] = 0.0f;
   }
-  __syncthreads();
+  group_sync(bar_id);
   auto issue = [&](int c) {
+    const unsigned st = (it0 + c) & 1;
     int m0 = c * BP2_MC, nm = min(BP2_MC, a.n_mu - m0);
-    uint64_t *bar = &bars[c & 1];
+    uint64_t *bar = &bars[st];
     dc::fence_proxy_async();
     dc::mbar_arrive_expect_tx(bar, (unsigned)(nm * a.NSp * 4));
     for (int q = 0; q < nm; ++q)
-      dc::bulk_g2s(smem + (c & 1) * stage_sz + (size_t)q * rstride + PADL, src + (size_t)(m0 + q) * a.NSp,
+      dc::bulk_g2s(smem + st * stage_sz + (size_t)q * rstride + PADL, src + (size_t)(m0 + q) * a.NSp,
                    (unsigned)(a.NSp * 4), bar);
   };
   // per-angle constants of this tile, from exact float splits of the origin
   auto angle_consts = [&](int c) {
-    int mi = threadIdx.x;
+    int mi = gt;
     int m = c * BP2_MC + mi;
     if (mi < BP2_MC && m < a.n_mu) {
       const dc::MuRec R = a.mu[m];
@@ -505,16 +541,16 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
       M.lo = -1.0f - I00;
       M.hi = (float)a.n_s - I00;
       M.cbase = (unsigned)((mi * rstride + PADL + (int)I00) * 4) - 4u * 0x4B400000u;
-      float ex = (float)(BP2_TX - 1) * M.Bc, ey = (float)(BP2_TY - 1) * M.Bs;
+      float ex = (float)(BP2_TX - 1) * M.Bc, ey = (float)(TY - 1) * M.Bs;
       float xmin = M.F00 + fminf(ex, 0.0f) + fminf(ey, 0.0f);
       float xmax = M.F00 + fmaxf(ex, 0.0f) + fmaxf(ey, 0.0f);
       M.fast = (xmin >= M.lo + 0.01f && xmax <= M.hi - 0.01f) ? 1 : 0;
       M.row0 = mi * rstride + PADL + (int)I00;
       M.pad1 = M.pad2 = 0;
-      bmu[c & 1][mi] = M;
+      bmu[(it0 + c) & 1][mi] = M;
     }
   };
-  if (threadIdx.x == 0) {
+  if (gt == 0) {
     issue(0);
     if (nchunk > 1) issue(1);
   }
@@ -525,15 +561,15 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
   // of sm_100+ (one issue slot for both); every component is rounded as the
   // scalar operation would round it
   static_assert(BP2_NQ == 2, "two pixels per thread and row, packed");
-  float2 acc[BP2_RY];
+  float2 acc[RY];
 #pragma unroll
-  for (int ry = 0; ry < BP2_RY; ++ry) acc[ry] = make_float2(0.0f, 0.0f);
-  const float rl0 = (float)(warp * BP2_RY);
-  float jlf[BP2_NQ], rlf[BP2_RY];  // pixel offsets inside the tile, as floats
+  for (int ry = 0; ry < RY; ++ry) acc[ry] = make_float2(0.0f, 0.0f);
+  const float rl0 = (float)(warp * RY);
+  float jlf[BP2_NQ], rlf[RY];  // pixel offsets inside the tile, as floats
 #pragma unroll
   for (int q = 0; q < BP2_NQ; ++q) jlf[q] = (float)(lane + 32 * q);
 #pragma unroll
-  for (int ry = 0; ry < BP2_RY; ++ry) rlf[ry] = rl0 + (float)ry;
+  for (int ry = 0; ry < RY; ++ry) rlf[ry] = rl0 + (float)ry;
   const float2 jl2 = make_float2(jlf[0], jlf[1]);
   const float2 mM2 = make_float2(-12582912.0f, -12582912.0f);  // -1.5 * 2^23
   const float2 M2 = make_float2(12582912.0f, 12582912.0f);
@@ -541,25 +577,26 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
 
   bool ok = true;
   for (int c = 0; c < nchunk; ++c) {
+    const unsigned st = (it0 + c) & 1;
     if (c + 1 < nchunk) angle_consts(c + 1);
-    if (!dc::mbar_wait_bounded(&bars[c & 1], (c >> 1) & 1, a.err)) ok = false;
-    if (__syncthreads_or(!ok)) {
+    if (!dc::mbar_wait_bounded(&bars[st], ((it0 + c) >> 1) & 1, a.err)) ok = false;
+    if (group_sync_or(bar_id, !ok)) {
       ok = false;
       break;
     }
-    const unsigned st_off = (unsigned)((c & 1) * stage_sz * 4);  // bytes
+    const unsigned st_off = st * (unsigned)(stage_sz * 4);  // bytes
     int nm = min(BP2_MC, a.n_mu - c * BP2_MC);
 #pragma unroll 2
     for (int mi = 0; mi < nm; ++mi) {
-      const BPMu M = bmu[c & 1][mi];
+      const BPMu M = bmu[st][mi];
       const unsigned cb = M.cbase + st_off;
       if (MULTI) {
         // taps k = floor(x) - 2 .. floor(x) + 3 (relative to I00) inside the
         // s range [lo + 1, hi - 1]; weight max(0, 1 - winv |x - k|)
-        const float *row = smem + (c & 1) * stage_sz + M.row0;
+        const float *row = smem + st * stage_sz + M.row0;
         const int klo = (int)M.lo + 1, khi = (int)M.hi - 1;
 #pragma unroll
-        for (int ry = 0; ry < BP2_RY; ++ry) {
+        for (int ry = 0; ry < RY; ++ry) {
           float rt = fmaf(rlf[ry], M.Bs, M.F00);
 #pragma unroll
           for (int q = 0; q < BP2_NQ; ++q) {
@@ -582,7 +619,7 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
         // below at 0 is a saturation to [0, 1]
         const float2 Bc2 = make_float2(M.Bc, M.Bc);
 #pragma unroll
-        for (int ry = 0; ry < BP2_RY; ++ry) {
+        for (int ry = 0; ry < RY; ++ry) {
           const float rt = fmaf(rlf[ry], M.Bs, M.F00);
           float2 x = __ffma2_rn(jl2, Bc2, make_float2(rt, rt));
           if (!M.fast)
@@ -603,18 +640,19 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
         }
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && c + 2 < nchunk) issue(c + 2);
+    group_sync(bar_id);
+    if (gt == 0 && c + 2 < nchunk) issue(c + 2);
   }
+  it = it0 + (unsigned)nchunk;
   if (!ok) {
-    for (int s = 0; s < 2; ++s) dc::mbar_wait_bounded(&bars[s], 0, nullptr);
-    return;
+    for (int s2 = 0; s2 < 2; ++s2) dc::mbar_wait_bounded(&bars[s2], 0, nullptr);
+    return false;
   }
 
   float lmax = 0.0f;
 #pragma unroll
-  for (int ry = 0; ry < BP2_RY; ++ry) {
-    int r = r0 + warp * BP2_RY + ry;
+  for (int ry = 0; ry < RY; ++ry) {
+    int r = r0 + warp * RY + ry;
 #pragma unroll
     for (int q = 0; q < BP2_NQ; ++q) {
       int j = j0 + lane + 32 * q;
@@ -626,7 +664,7 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
         val *= (a.weight == WT_D) ? l2 : fv.D * rsqrtf(l2);
       }
       if (a.out_kind == OUT_F32_ABSMAX) {
-        ((float *)a.out)[((size_t)n * a.H + r) * a.Wp + j] = val;
+        ((float *)a.out)[((size_t)slot * a.H + r) * a.Wp + j] = val;
         lmax = fmaxf(lmax, fabsf(val));
       } else {
         size_t o = (((size_t)b * a.V + v) * a.H + r) * a.W + j;
@@ -639,8 +677,25 @@ __global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
   }
   if (a.out_kind == OUT_F32_ABSMAX) {
     for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-    if (lane == 0) atomicMax(&a.absmax[n], __float_as_uint(lmax));
+    if (lane == 0) atomicMax(&a.absmax[slot], __float_as_uint(lmax));
   }
+  return true;
+}
+
+template <bool MULTI>
+__global__ void __launch_bounds__(BP2_THREADS) k_bp2d(BP2Args a) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ uint64_t bars[2];
+  __shared__ BPMu bmu[2][BP2_MC];
+  if (threadIdx.x == 0) {
+    dc::mbar_init(&bars[0], 1);
+    dc::mbar_init(&bars[1], 1);
+    dc::fence_barrier_init();
+  }
+  __syncthreads();
+  unsigned it = 0;
+  bp2d_tile<MULTI, BP2_RY>(a, blockIdx.z, blockIdx.z, blockIdx.x, blockIdx.y, threadIdx.x, 0, smem,
+                           bars, bmu, it);
 }
 
 // FP16 storage with a per-view power-of-two scale chosen from the absmax so
@@ -759,9 +814,9 @@ size_t linesum_smem_for(int H, int W, int mg, int NSp, int rb) {
 }
 
 // tallest band whose two stages fit the shared-memory budget (0: none)
-int linesum_band_rows(int H, int W, int mg, int NSp) {
+int linesum_band_rows(int H, int W, int mg, int NSp, size_t budget = LS_SMEM_BUDGET) {
   for (int rb = 32; rb >= 8; rb /= 2)
-    if (linesum_smem_for(H, W, mg, NSp, rb) <= LS_SMEM_BUDGET) return rb;
+    if (linesum_smem_for(H, W, mg, NSp, rb) <= budget) return rb;
   return 0;
 }
 
@@ -922,6 +977,153 @@ Chunking chunking(const dc_geometry *g, int B, int view_limit = 0) {
   return c;
 }
 
+// ------------------------------------------------ batched persistent filter
+// One kernel filters every view of a batch of problems (orbits with uneven
+// view counts, detectors and angle grids): persistent CTAs of BF_THREADS
+// threads, one per SM, take (problem, view) items from a device counter.  An
+// item is a whole image: its weighted copy (w_cos, rows padded) goes to the
+// CTA's own image scratch, the line sums of every angle group fill the CTA's
+// sinogram scratch (the M_FILTER epilogue: D_f, w_sino, W K, D_b), and the
+// 2-D backprojection of that sinogram (w_d epilogue) is computed by the
+// CTA's two halves, each a group of BP2_THREADS threads with its own stages,
+// mbarriers and named barrier, taking alternate pixel tiles.  FP16 storage
+// keeps the FP32 result in the image scratch, then converts it with the
+// image's power-of-two scale.
+constexpr int BF_THREADS = 512;
+static_assert(BF_THREADS == 2 * BP2_THREADS, "two 2-D backprojection groups per CTA");
+// rows per warp of the 2-D backprojection tiles here: with one CTA per SM a
+// warp keeps 16 pixels in flight (64 x 64 tiles) to hide latency with half
+// the warps of the standalone kernel's four CTAs per SM
+constexpr int BF_RY = 8;
+constexpr int DC_BF_MAX = 32;
+
+struct FilterProblem {
+  LineArgs la;          // the geometry's tables; img, out and Wred are set per CTA / run
+  BP2Args ba;           // out = the problem's g^F; sino, absmax and out (FP16) per CTA
+  long long first;      // first item (view 0) of this problem
+  int rb;               // line-sum band rows (32, 16, 8)
+  int n_groups;         // angle groups of the line sums
+  int multi;            // ds < pitch: the bounds-checked multi-tap 2-D backprojection
+  int tiles_x, tiles_y;
+  int dtype;            // DC_F32 / DC_BF16 / DC_F16
+  float *scale;         // [V] FP16 scales
+};
+
+struct FilterRun {
+  const float *g[DC_BF_MAX];   // [V][H][W] projections of each table entry
+  const float *W[DC_BF_MAX];   // [V][n_mu][n_s] weights or NULL (= 1/2)
+};
+
+template <int RB>
+__device__ __forceinline__ void linesum_all_groups(const LineArgs &la, int v, int n_groups,
+                                                   float *smem, LineMu *lmu, short2 *ttab) {
+  for (int gi = 0; gi < n_groups; ++gi) {
+    linesum_body<M_FILTER, RB, BF_THREADS>(la, gi, v, 0, smem, lmu, ttab);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(BF_THREADS, 1)
+    k_filter_batched(const FilterProblem *__restrict__ probs, int nprob, long long total,
+                     unsigned long long *counter, FilterRun run, float *img_scratch,
+                     size_t img_cap, float *sino_scratch, size_t sino_cap,
+                     unsigned *absmax_scratch, int bp2_floats) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ LineMu lmu[dc::DC_LS_MAX_MG];
+  __shared__ short2 ttab[dc::DC_LS_MAX_TASKS];
+  __shared__ uint64_t bars[2][2];
+  __shared__ BPMu bmu[2][2][BP2_MC];
+  __shared__ long long item;
+  __shared__ int failed;
+  const int tid = threadIdx.x, grp = tid / BP2_THREADS, gt = tid % BP2_THREADS;
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      dc::mbar_init(&bars[q][0], 1);
+      dc::mbar_init(&bars[q][1], 1);
+    }
+    dc::fence_barrier_init();
+    failed = 0;
+  }
+  float *img = img_scratch + (size_t)blockIdx.x * img_cap;
+  float *sino = sino_scratch + (size_t)blockIdx.x * sino_cap;
+  unsigned *amax = absmax_scratch + blockIdx.x;
+  unsigned it = 0;  // angle chunks staged by this thread's group
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) item = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const long long w = item;
+    if (w >= total || failed) break;
+    int p = 0;
+    while (p + 1 < nprob && probs[p + 1].first <= w) ++p;
+    const FilterProblem &P = probs[p];
+    const int v = (int)(w - P.first);
+    LineArgs la = P.la;
+    la.img = img;
+    la.out = sino;
+    la.Wred = run.W[p];
+    BP2Args ba = P.ba;
+    ba.sino = sino;
+    ba.absmax = amax;
+    if (P.dtype == DC_F16) ba.out = img;
+
+    // w_cos g of view v into the image scratch, rows padded to Wp with zeros
+    {
+      const dc::FView f = la.fv[v];
+      const float *src = run.g[p] + (size_t)v * la.H * la.W;
+      for (int r = tid / 32; r < la.H; r += BF_THREADS / 32)
+        for (int j = tid % 32; j < la.Wp; j += 32) {
+          float val = 0.0f;
+          if (j < la.W) {
+            const float x = (j - f.cu) * la.pitch, y = (r - f.cv) * la.pitch;
+            val = src[(size_t)r * la.W + j] * (f.D * rsqrtf(fmaf(x, x, fmaf(y, y, f.D * f.D))));
+          }
+          img[(size_t)r * la.Wp + j] = val;
+        }
+    }
+    if (tid == 0) *amax = 0u;
+    __syncthreads();
+    switch (P.rb) {
+      case 32: linesum_all_groups<32>(la, v, P.n_groups, smem, lmu, ttab); break;
+      case 16: linesum_all_groups<16>(la, v, P.n_groups, smem, lmu, ttab); break;
+      default: linesum_all_groups<8>(la, v, P.n_groups, smem, lmu, ttab); break;
+    }
+    // the sinogram was written by ordinary stores and is read back by bulk
+    // (async-proxy) copies
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    const int ntiles = P.tiles_x * P.tiles_y;
+    float *gsm = smem + (size_t)grp * bp2_floats;
+    bool ok = true;
+    for (int t = grp; t < ntiles && ok; t += 2) {
+      ok = P.multi ? bp2d_tile<true, BF_RY>(ba, v, 0, t % P.tiles_x, t / P.tiles_x, gt, 1 + grp,
+                                            gsm, bars[grp], bmu[grp], it)
+                   : bp2d_tile<false, BF_RY>(ba, v, 0, t % P.tiles_x, t / P.tiles_x, gt, 1 + grp,
+                                             gsm, bars[grp], bmu[grp], it);
+    }
+    if (!ok) failed = 1;
+    __syncthreads();
+    if (failed) break;
+    if (P.dtype == DC_F16) {
+      // power-of-two scale mapping the view's absmax into [2^14, 2^15)
+      const float am = __uint_as_float(*(volatile unsigned *)amax);
+      float sc = 1.0f;
+      if (am > 0.0f) {
+        int e;
+        frexpf(am, &e);
+        sc = ldexpf(1.0f, e - 15);
+      }
+      if (tid == 0) P.scale[v] = sc;
+      const float inv = 1.0f / sc;
+      __half *dst = (__half *)P.ba.out + (size_t)v * la.H * la.W;
+      for (int r = tid / 32; r < la.H; r += BF_THREADS / 32)
+        for (int j = tid % 32; j < la.W; j += 32)
+          dst[(size_t)r * la.W + j] = __float2half_rn(img[(size_t)r * la.Wp + j] * inv);
+    }
+  }
+  // nothing is left in flight: every staged chunk was waited for
+}
+
 }  // namespace
 
 namespace dc {
@@ -1005,6 +1207,137 @@ int filter_chunk(const dc_geometry *g, const float *gin, const float *W, void *g
     ba.out = gF;
     if ((rc = launch_bp2d(g, ba, st))) return rc;
   }
+  return DC_OK;
+}
+
+// The plan of the batched persistent filter: the problem table (in the
+// order the items are handed out: largest per-image work first), the per-CTA
+// scratch and the launch shape.
+struct BatchFilterPlan {
+  int n;
+  int grid;
+  long long total;
+  size_t smem, img_cap, sino_cap;
+  int bp2_floats;
+  int order[DC_BF_MAX];  // table position -> problem index
+  FilterProblem *d_probs;
+  unsigned long long *d_counter;
+  float *img_scratch, *sino_scratch;
+  unsigned *amax;
+};
+
+void batch_filter_destroy(BatchFilterPlan *p) {
+  if (!p) return;
+  cudaFree(p->d_probs);
+  cudaFree(p->d_counter);
+  cudaFree(p->img_scratch);
+  cudaFree(p->sino_scratch);
+  cudaFree(p->amax);
+  delete p;
+}
+
+int batch_filter_create(int n, dc_geometry *const *geoms, int dtype, void *const *gF,
+                        float *const *scale, BatchFilterPlan **out) {
+  *out = nullptr;
+  if (n < 1 || n > DC_BF_MAX) return fail(DC_ERR_ARG, "batched filter: 1 <= n <= 32");
+  int dev = 0;
+  DC_CUDA(cudaGetDevice(&dev));
+  cudaFuncAttributes fa;
+  DC_CUDA(cudaFuncGetAttributes(&fa, k_filter_batched));
+  int optin = 0;
+  DC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t budget = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  BatchFilterPlan *p = new BatchFilterPlan();
+  memset((void *)p, 0, sizeof(BatchFilterPlan));
+  p->n = n;
+  // largest per-image work first (line-sum steps plus 2-D backprojection pairs)
+  auto work = [&](int i) {
+    const dc_geometry_desc &d = geoms[i]->d;
+    return (double)d.n_mu * d.n_s * std::max(d.det_rows, d.det_cols) +
+           (double)d.det_rows * d.det_cols * d.n_mu;
+  };
+  for (int i = 0; i < n; ++i) p->order[i] = i;
+  std::stable_sort(p->order, p->order + n, [&](int x, int y) { return work(x) > work(y); });
+  std::vector<FilterProblem> probs(n);
+  long long first = 0;
+  for (int t = 0; t < n; ++t) {
+    const dc_geometry *g = geoms[p->order[t]];
+    const dc_geometry_desc &d = g->d;
+    FilterProblem &P = probs[t];
+    memset((void *)&P, 0, sizeof(P));
+    P.la = line_args(g, 1, 0, 0, 1);
+    P.ba = bp2_args(g, 1, 0, 0, 1, nullptr);
+    P.ba.weight = WT_D;
+    P.ba.out_kind = (dtype == DC_BF16) ? OUT_BF16 : (dtype == DC_F16 ? OUT_F32_ABSMAX : OUT_F32);
+    P.ba.out = gF[p->order[t]];
+    P.rb = linesum_band_rows(d.det_rows, d.det_cols, g->mg, g->NSp, budget);
+    P.n_groups = g->n_groups;
+    P.multi = multi_tap(g) ? 1 : 0;
+    P.tiles_x = (d.det_cols + BP2_TX - 1) / BP2_TX;
+    P.tiles_y = (d.det_rows + 8 * BF_RY - 1) / (8 * BF_RY);
+    P.dtype = dtype;
+    P.scale = (dtype == DC_F16) ? scale[p->order[t]] : nullptr;
+    P.first = first;
+    first += d.n_views;
+    if (P.rb == 0) {
+      batch_filter_destroy(p);
+      return fail(DC_ERR_UNSUPPORTED, "batched filter: detector rows too long for its shared memory");
+    }
+    p->img_cap = std::max(p->img_cap, (size_t)d.det_rows * g->Wp);
+    p->sino_cap = std::max(p->sino_cap, (size_t)d.n_mu * g->NSp);
+    p->bp2_floats = std::max(p->bp2_floats, 2 * BP2_MC * (g->NSp + PADL + PADR));
+    p->smem = std::max(p->smem, linesum_smem_for(d.det_rows, d.det_cols, g->mg, g->NSp, P.rb));
+  }
+  p->total = first;
+  p->smem = std::max(p->smem, (size_t)2 * p->bp2_floats * sizeof(float));
+  if (p->smem > budget) {
+    batch_filter_destroy(p);
+    return fail(DC_ERR_UNSUPPORTED, "batched filter: sinogram rows too long for its shared memory");
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_filter_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)p->smem);
+  int per_sm = 0, sms = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batched, BF_THREADS, p->smem);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    batch_filter_destroy(p);
+    return cuda_fail(e, "batched filter: launch shape");
+  }
+  if (per_sm < 1) {
+    batch_filter_destroy(p);
+    return fail(DC_ERR_UNSUPPORTED, "batched filter: no resident CTA fits");
+  }
+  p->grid = std::max(1, sms) * per_sm;
+  e = dmalloc((void **)&p->d_probs, sizeof(FilterProblem) * n);
+  if (e == cudaSuccess) e = dmalloc((void **)&p->d_counter, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = dmalloc((void **)&p->img_scratch, sizeof(float) * p->img_cap * p->grid);
+  if (e == cudaSuccess) e = dmalloc((void **)&p->sino_scratch, sizeof(float) * p->sino_cap * p->grid);
+  if (e == cudaSuccess) e = dmalloc((void **)&p->amax, sizeof(unsigned) * p->grid);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_probs, probs.data(), sizeof(FilterProblem) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    batch_filter_destroy(p);
+    return cuda_fail(e, "batched filter: allocation");
+  }
+  *out = p;
+  return DC_OK;
+}
+
+int batch_filter_run(BatchFilterPlan *p, const float *const *g, const float *const *W,
+                     cudaStream_t st) {
+  FilterRun run;
+  memset(&run, 0, sizeof(run));
+  for (int t = 0; t < p->n; ++t) {
+    run.g[t] = g[p->order[t]];
+    run.W[t] = W ? W[p->order[t]] : nullptr;
+  }
+  DC_CUDA(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), st));
+  ProfScope ps(KID_FILTER_BATCHED, st);
+  k_filter_batched<<<p->grid, BF_THREADS, p->smem, st>>>(
+      p->d_probs, p->n, p->total, p->d_counter, run, p->img_scratch, p->img_cap, p->sino_scratch,
+      p->sino_cap, p->amax, p->bp2_floats);
+  DC_CHECK_LAUNCH("k_filter_batched");
   return DC_OK;
 }
 

@@ -55,8 +55,13 @@ def test_batched_matches_oracle(dtype, tol):
     batch.close()
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
-def test_batched_equals_per_problem_calls(dtype):
+# The batched filter computes the 2-D backprojection in taller pixel tiles
+# than the per-problem calls, so the s-bin positions are taken from other
+# tile origins and g^F agrees to FP32 rounding (FP32: ~1e-7 after the
+# backprojection); stored in 16 bits, a few values then round the other way
+# (one BF16 / FP16 step is 2^-8 / 2^-11 of the value), ~1e-5 in the volume.
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-6), ("bf16", 1e-4), ("f16", 2e-5)])
+def test_batched_equals_per_problem_calls(dtype, tol):
     probs = _problems()
     geoms = [p[1] for p in probs]
     g_list = [p[2] for p in probs]
@@ -68,7 +73,7 @@ def test_batched_equals_per_problem_calls(dtype):
         ref = api.dc_backproject(geom, gF, sc, kahan=(dtype != "f32"))[0]
         torch.cuda.synchronize()
         assert torch.isfinite(v).all()
-        assert rel_l2(v.double().cpu().numpy(), ref.double().cpu().numpy()) < 1e-6
+        assert rel_l2(v.double().cpu().numpy(), ref.double().cpu().numpy()) < tol
     for geom in geoms:
         api.dc_sync_status(geom)
     batch.close()
