@@ -443,7 +443,7 @@ def batched_measure(args, dev, L):
            "volumes": [w.vol_shape[0] for w in ws], "voxel_view_updates": updates}
     for dtype in ("f32", "bf16"):
         batch = api.Batch(geoms, dtype=dtype, kahan=(dtype != "f32"))
-        tuned = tune.autotune_batch(batch, g_list, vols)
+        tuned = tune.autotune_batch(batch, g_list, vols, dtype=dtype, kahan=(dtype != "f32"))
         batch.capture(g_list, vols)
         ms = timed(batch.replay, args.steps)
         out[f"{dtype}_graph_ms_per_batch"] = ms

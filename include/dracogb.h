@@ -279,8 +279,15 @@ int dc_gauss_smooth(int V, int n_mu, int n_s, float sigma, int radius, int adjoi
  *   vol[i]: device [Z_i][Y_i][X_i] FP32, overwritten.  Allocates nothing, so
  *   a run can be captured in a CUDA graph and replayed with the same
  *   pointers.  Uses each geometry's work area: one run at a time per batch.
- * dc_batch_set_bp_nz -- voxels per thread along z in the backprojection
- *   (16 or 32), for the autotuner.
+ * dc_batch_set_bp_nz -- voxels per thread along z in the backprojection:
+ *   16 or 32 for every problem, or 0 (the default) for each geometry's own
+ *   bp_nz (dc_geometry_set_tuning), for the autotuner.
+ *
+ * The run is two persistent launches: a filter kernel whose CTAs (one per
+ * SM) take (problem, view) images from a device counter, largest per-image
+ * work first, and the backprojection kernel over (problem, voxel box)
+ * items.  Problems whose detector or sinogram rows do not fit the filter
+ * kernel's shared memory are filtered by per-problem dc_filter calls.
  */
 typedef struct dc_batch dc_batch;
 int dc_batch_create(int n, dc_geometry *const *geoms, int dtype, unsigned flags,

@@ -631,13 +631,14 @@ struct BatchProblem {
   const CUtensorMap *tmn; // global-memory tensor maps over the problem's g^F
   const CUtensorMap *tmw;
   int bx, by, bz;         // boxes per dimension (bz includes the batch)
+  int nz;                 // voxels per thread along z (box depth) of this problem: 16 or 32
   long long first;        // first work item of this problem
 };
 struct BatchRun {
   float *vol[DC_MAX_BATCH];
 };
 
-template <typename T, bool KAHAN, int NZ>
+template <typename T, bool KAHAN>
 __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_batched(const BatchProblem *probs,
                                                                  int nprob, long long total,
                                                                  unsigned long long *counter,
@@ -667,8 +668,14 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_batched(const BatchPro
     long long rest = lw / P.bx;
     int byi = (int)(rest % P.by);
     int bzi = (int)(rest / P.by);
-    if (!bp_box<T, KAHAN, NZ>(P.a, run.vol[p], P.tmn, P.tmw, err, bxi, byi, bzi, dsm, full, sv,
-                              vtab, it)) {
+    // each problem has its own box depth (the autotuner's choice for its
+    // detector-to-voxel scale); the CTA-uniform branch picks the instance
+    const bool done = (P.nz == 16)
+                          ? bp_box<T, KAHAN, 16>(P.a, run.vol[p], P.tmn, P.tmw, err, bxi, byi, bzi,
+                                                 dsm, full, sv, vtab, it)
+                          : bp_box<T, KAHAN, 32>(P.a, run.vol[p], P.tmn, P.tmw, err, bxi, byi, bzi,
+                                                 dsm, full, sv, vtab, it);
+    if (!done) {
       for (int q = 0; q < TB_NS; ++q) dc::mbar_wait_bounded(&full[q], 0, nullptr);
       return;
     }
@@ -1141,7 +1148,7 @@ struct dc_batch {
   int n;
   int dtype;
   unsigned flags;
-  int nz;
+  int nz;                         // 16 / 32 for every problem, 0: each geometry's own bp_nz
   int grid;
   long long total;
   int order[DC_MAX_BATCH];        // table position -> problem index
@@ -1204,7 +1211,8 @@ int build_batch_tables(dc_batch *b) {
     P.tmw = b->d_maps + 2 * t + 1;
     P.bx = (d.vol_x + TB_TX - 1) / TB_TX;
     P.by = (d.vol_y + TB_TY - 1) / TB_TY;
-    P.bz = (d.vol_z + b->nz - 1) / b->nz;
+    P.nz = b->nz ? b->nz : g->bp_nz;
+    P.bz = (d.vol_z + P.nz - 1) / P.nz;
     P.first = first;
     first += (long long)P.bx * P.by * P.bz;
   }
@@ -1216,22 +1224,20 @@ int build_batch_tables(dc_batch *b) {
   return DC_OK;
 }
 
-template <typename T, bool KAHAN, int NZ>
+template <typename T, bool KAHAN>
 int launch_batched(dc_batch *b, BatchRun &run, cudaStream_t st) {
   const size_t sm = bp_tma_smem<T>();
-  DC_CUDA(cudaFuncSetAttribute(k_bp3d_batched<T, KAHAN, NZ>,
+  DC_CUDA(cudaFuncSetAttribute(k_bp3d_batched<T, KAHAN>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_bp3d_batched<T, KAHAN, NZ><<<b->grid, dim3(TB_TX, TB_TY), sm, st>>>(
+  k_bp3d_batched<T, KAHAN><<<b->grid, dim3(TB_TX, TB_TY), sm, st>>>(
       b->d_probs, b->n, b->total, b->d_counter, b->geoms[0]->w_flags, run);
   return DC_OK;
 }
 
 template <typename T>
 int launch_batched_t(dc_batch *b, BatchRun &run, cudaStream_t st) {
-  bool kahan = (b->flags & DC_KAHAN) != 0;
-  if (b->nz == 16)
-    return kahan ? launch_batched<T, true, 16>(b, run, st) : launch_batched<T, false, 16>(b, run, st);
-  return kahan ? launch_batched<T, true, 32>(b, run, st) : launch_batched<T, false, 32>(b, run, st);
+  return (b->flags & DC_KAHAN) ? launch_batched<T, true>(b, run, st)
+                               : launch_batched<T, false>(b, run, st);
 }
 
 }  // namespace
@@ -1265,7 +1271,7 @@ int dc_batch_create(int n, dc_geometry *const *geoms, int dtype, unsigned flags,
   b->n = n;
   b->dtype = dtype;
   b->flags = flags;
-  b->nz = 32;
+  b->nz = 0;  // each problem's box depth from its geometry (dc_geometry_set_tuning)
   for (int i = 0; i < n; ++i) b->geoms[i] = geoms[i];
   // largest view count first
   for (int i = 0; i < n; ++i) b->order[i] = i;
@@ -1308,9 +1314,8 @@ int dc_batch_create(int n, dc_geometry *const *geoms, int dtype, unsigned flags,
 }
 
 int dc_batch_set_bp_nz(dc_batch *b, int nz) {
-  if (!b || (nz != 16 && nz != 32))
-    return dc::fail(DC_ERR_ARG, "dc_batch_set_bp_nz: nz must be 16 or 32");
-  if (b->nz == nz) return DC_OK;
+  if (!b || (nz != 0 && nz != 16 && nz != 32))
+    return dc::fail(DC_ERR_ARG, "dc_batch_set_bp_nz: nz must be 16, 32 or 0 (per geometry)");
   b->nz = nz;
   return build_batch_tables(b);
 }

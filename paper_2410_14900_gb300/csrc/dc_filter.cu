@@ -994,7 +994,7 @@ static_assert(BF_THREADS == 2 * BP2_THREADS, "two 2-D backprojection groups per 
 // rows per warp of the 2-D backprojection tiles here: with one CTA per SM a
 // warp keeps 16 pixels in flight (64 x 64 tiles) to hide latency with half
 // the warps of the standalone kernel's four CTAs per SM
-constexpr int BF_RY = 8;
+constexpr int BF_RY = 16;
 constexpr int DC_BF_MAX = 32;
 
 struct FilterProblem {

@@ -100,12 +100,21 @@ def autotune(geom: api.Geometry, dtype: str = "f32", use_cache: bool = True,
     return dict(best, cached=False)
 
 
-def autotune_batch(batch: "api.Batch", g_list, vol_list, nzs=(16, 32)) -> dict:
-    """Pick the batch backprojection's voxels per thread along z."""
+def autotune_batch(batch: "api.Batch", g_list, vol_list, nzs=(16, 32), dtype: str = "f32",
+                   kahan: bool = False) -> dict:
+    """Pick the batch backprojection's voxels per thread along z: one depth
+    for every problem, or each problem's own (0: the depth `autotune` picks
+    for that geometry alone), whichever runs the batch fastest."""
+    per = {}
+    for gm in batch.geoms:
+        t = api.dc_geometry_get_tuning(gm)
+        r = autotune(gm, dtype, chunks=(t["chunk_images"],), nzs=nzs, kahan=kahan)
+        per[shape_key(gm, dtype)] = r["bp_nz"]
     times = {}
-    for nz in nzs:
+    for nz in (0,) + tuple(nzs):
         batch.set_bp_nz(nz)
         times[nz] = _time(lambda: batch.run(g_list, vol_list))
     best = min(times, key=times.get)
     batch.set_bp_nz(best)
-    return {"bp_nz": int(best), "run_ms": {str(k): v for k, v in times.items()}}
+    return {"bp_nz": int(best), "per_problem_nz": per,
+            "run_ms": {str(k): v for k, v in times.items()}}

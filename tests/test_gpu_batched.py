@@ -87,7 +87,7 @@ def test_batched_graph_replay_and_weights():
     batch = api.Batch(geoms)
     tuned = tune.autotune_batch(batch, g_list, [torch.empty(gm.vol_shape, device="cuda")
                                                 for gm in geoms])
-    assert tuned["bp_nz"] in (16, 32)
+    assert tuned["bp_nz"] in (0, 16, 32)   # 0: each problem's own depth
     vols = [torch.zeros(geom.vol_shape, device="cuda") for geom in geoms]
     batch.capture(g_list, vols, W_list)
     for v in vols:
