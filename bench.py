@@ -220,24 +220,49 @@ def oracle_sample(w, g_np, n_views_sample: int, n_vox_sample: int, seed: int = 0
 def oracle_full(names=("circle64", "sinusoid256"), device=None) -> dict:
     """The FP64 oracle's complete reconstruction (Eq. 12, no sampling) of the
     two smaller configurations: 64-view circle 64^2 -> 64^3 and 360-view
-    sinusoid 256^2 -> 256^3, timed on the host cores (the input projections
-    are generated beforehand, on `device` if given, outside the timing)."""
+    sinusoid 256^2 -> 256^3 with Poisson noise, timed on the host cores (the
+    input projections are generated beforehand, on `device` if given,
+    outside the timing).  With a device, the CUDA reconstruction of the same
+    FP32-rounded input is timed beside it (CUDA events, 5 runs after 2
+    warm-up runs) and compared with the oracle's volume (relative L2)."""
     import torch
     from oracle import oracle as orc
-    from paper_2410_14900_gb300 import synth
+    from paper_2410_14900_gb300 import api, synth
     out = {}
     for name in names:
         w = synth.workload(name)
         og = orc.Geometry(w.desc_dict(), w.matrices(), w.orbit.vdl)
         g = synth.project_phantom(w.phantoms()[0], w.orbit, w.det_rows, w.det_cols, w.pitch,
                                   device=device, dtype=torch.float64)
+        if w.photons:
+            g = synth.add_poisson_noise(g, w.photons, 0.02, seed=w.seed)
         if device is not None:
             g = g.cpu().numpy()
+        g32 = g.astype(np.float32).astype(np.float64)
         t0 = time.perf_counter()
-        orc.reconstruct(og, g[None])
-        out[name] = {"ms_per_volume": 1e3 * (time.perf_counter() - t0), "views": w.n_views,
-                     "detector": [w.det_rows, w.det_cols], "volume": list(w.vol_shape),
-                     "extrapolated": False}
+        ref = orc.reconstruct(og, g32[None])
+        rec = {"ms_per_volume": 1e3 * (time.perf_counter() - t0), "views": w.n_views,
+               "detector": [w.det_rows, w.det_cols], "volume": list(w.vol_shape),
+               "extrapolated": False}
+        if device is not None:
+            geom = api.Geometry(w.desc_dict(), w.matrices(), w.orbit.vdl)
+            gt = torch.as_tensor(g32, device=device, dtype=torch.float32)[None].contiguous()
+            for _ in range(2):
+                vol = api.reconstruct(geom, gt)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                vol = api.reconstruct(geom, gt)
+            e1.record()
+            torch.cuda.synchronize()
+            v = vol.double().cpu().numpy()
+            rec["gpu_ms_per_volume"] = e0.elapsed_time(e1) / 5
+            rec["gpu_rel_l2_vs_oracle"] = float(np.linalg.norm(v - ref) / np.linalg.norm(ref))
+            api.dc_sync_status(geom)
+            geom.close()
+        out[name] = rec
     return out
 
 
@@ -441,15 +466,18 @@ def batched_measure(args, dev, L):
     out = {"problems": len(ws), "views": [w.n_views for w in ws],
            "detectors": [[w.det_rows, w.det_cols] for w in ws],
            "volumes": [w.vol_shape[0] for w in ws], "voxel_view_updates": updates}
-    for dtype in ("f32", "bf16"):
-        batch = api.Batch(geoms, dtype=dtype, kahan=(dtype != "f32"))
+    for dtype, persistent in (("f32", False), ("bf16", False), ("f32", True)):
+        batch = api.Batch(geoms, dtype=dtype, kahan=(dtype != "f32"),
+                          persistent_filter=persistent)
         tuned = tune.autotune_batch(batch, g_list, vols, dtype=dtype, kahan=(dtype != "f32"))
         batch.capture(g_list, vols)
         ms = timed(batch.replay, args.steps)
-        out[f"{dtype}_graph_ms_per_batch"] = ms
-        out[f"{dtype}_bp_nz"] = tuned["bp_nz"]
+        tag = dtype + ("_persistent_filter" if persistent else "")
+        out[f"{tag}_graph_ms_per_batch"] = ms
+        out[f"{tag}_bp_nz"] = tuned["bp_nz"]
         batch.close()
         del batch
+    # one by one, each problem with its own tuned box depth (set above)
     def seq():
         for gm, g, v in zip(geoms, g_list, vols):
             gF, _ = api.dc_filter(gm, g[None])

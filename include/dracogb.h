@@ -69,6 +69,8 @@ extern "C" {
 #define DC_ACCUM 1u           /* add into vol instead of overwriting        */
 #define DC_KAHAN 2u           /* compensated (Kahan) summation over views   */
 #define DC_RELU 4u            /* ReLU after the sum over views (Sec. 2.3)   */
+/* dc_batch_create flag: filter every problem in one persistent launch */
+#define DC_PERSISTENT_FILTER 8u
 
 /* maximum number of orbit segments of dc_crofton_weights */
 #define DC_MAX_SEGMENTS 16
@@ -272,8 +274,9 @@ int dc_gauss_smooth(int V, int n_mu, int n_s, float sigma, int radius, int adjoi
  *
  * dc_batch_create -- plans a batch of n <= 32 geometries (not owned; they
  *   must outlive the batch) for g^F storage `dtype` and flags DC_KAHAN |
- *   DC_RELU.  Allocates the batch's filtered projections and tables.  Every
- *   detector row must be a multiple of 16 bytes in `dtype` (tiled TMA loads).
+ *   DC_RELU | DC_PERSISTENT_FILTER.  Allocates the batch's filtered
+ *   projections and tables.  Every detector row must be a multiple of 16
+ *   bytes in `dtype` (tiled TMA loads).
  * dc_batch_run -- g[i]: device [V_i][H_i][W_i] FP32; W[i]: device
  *   [V_i][n_mu_i][n_s_i] or NULL entries (W itself may be NULL: all 1/2);
  *   vol[i]: device [Z_i][Y_i][X_i] FP32, overwritten.  Allocates nothing, so
@@ -283,11 +286,16 @@ int dc_gauss_smooth(int V, int n_mu, int n_s, float sigma, int radius, int adjoi
  *   16 or 32 for every problem, or 0 (the default) for each geometry's own
  *   bp_nz (dc_geometry_set_tuning), for the autotuner.
  *
- * The run is two persistent launches: a filter kernel whose CTAs (one per
- * SM) take (problem, view) images from a device counter, largest per-image
- * work first, and the backprojection kernel over (problem, voxel box)
- * items.  Problems whose detector or sinogram rows do not fit the filter
- * kernel's shared memory are filtered by per-problem dc_filter calls.
+ * The backprojection of a run is one persistent launch over (problem,
+ * voxel box) items.  The filter is, by default, each problem's dc_filter
+ * (chunked launches, recorded in the same graph); with
+ * DC_PERSISTENT_FILTER it is one persistent launch whose CTAs (one per SM)
+ * take (problem, view) images from a device counter, largest per-image
+ * work first, so the whole run is two persistent launches.  (On GB300 that
+ * kernel runs its 2-D backprojection at half the warps per SM of the
+ * chunked kernel and is ~11% slower; it is kept for launch-bound uses.)
+ * With the flag, problems whose detector or sinogram rows do not fit that
+ * kernel's shared memory fall back to the per-problem calls.
  */
 typedef struct dc_batch dc_batch;
 int dc_batch_create(int n, dc_geometry *const *geoms, int dtype, unsigned flags,

@@ -16,7 +16,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import DC_ACCUM, DC_BF16, DC_F16, DC_F32, DC_KAHAN, DC_RELU, check
+from ._lib import (DC_ACCUM, DC_BF16, DC_F16, DC_F32, DC_KAHAN, DC_PERSISTENT_FILTER, DC_RELU,
+                   check)
 
 _DTYPES = {"f32": (DC_F32, torch.float32), "bf16": (DC_BF16, torch.bfloat16),
            "f16": (DC_F16, torch.float16)}
@@ -325,11 +326,13 @@ class Batch:
     graph (capture()) and replayed (replay()).
     """
 
-    def __init__(self, geoms, dtype: str = "f32", kahan: bool = False, relu: bool = False):
+    def __init__(self, geoms, dtype: str = "f32", kahan: bool = False, relu: bool = False,
+                 persistent_filter: bool = False):
         L = _lib.load()
         self.geoms = list(geoms)
         arr = (ctypes.c_void_p * len(self.geoms))(*[g.handle for g in self.geoms])
-        flags = (DC_KAHAN if kahan else 0) | (DC_RELU if relu else 0)
+        flags = ((DC_KAHAN if kahan else 0) | (DC_RELU if relu else 0)
+                 | (DC_PERSISTENT_FILTER if persistent_filter else 0))
         h = ctypes.c_void_p()
         check(L.dc_batch_create(len(self.geoms), arr, _DTYPES[dtype][0], flags, ctypes.byref(h)),
               "dc_batch_create")

@@ -1139,8 +1139,9 @@ int dc_backproject_adjoint(const dc_geometry *g, int B, const float *grad_vol,
 }  // extern "C"
 
 // ------------------------------------------------------------------------
-// Batched reconstruction: one persistent filter kernel over the (problem,
-// view) images of all problems, then one persistent backprojection over all
+// Batched reconstruction: the filter of every problem (its chunked launches,
+// or with DC_PERSISTENT_FILTER one persistent kernel over the (problem,
+// view) images of all problems), then one persistent backprojection over all
 // problems' voxel boxes.  Everything a run needs is allocated by
 // dc_batch_create, so dc_batch_run allocates nothing and can be captured in
 // a CUDA graph.
@@ -1190,7 +1191,7 @@ int build_batch_tables(dc_batch *b) {
     P.a.scale = (b->dtype == DC_F16) ? b->scale[i] : nullptr;
     P.a.views = g->bpv;
     P.a.vol = nullptr;
-    P.a.flags = b->flags & ~DC_KAHAN;
+    P.a.flags = b->flags & DC_RELU;
     P.a.V = d.n_views;
     P.a.H = d.det_rows;
     P.a.W = d.det_cols;
@@ -1252,8 +1253,9 @@ int dc_batch_create(int n, dc_geometry *const *geoms, int dtype, unsigned flags,
     return dc::fail(DC_ERR_ARG, "dc_batch_create: 1 <= n <= " + std::to_string(DC_MAX_BATCH));
   if (dtype != DC_F32 && dtype != DC_BF16 && dtype != DC_F16)
     return dc::fail(DC_ERR_ARG, "dc_batch_create: unknown dtype");
-  if (flags & ~(DC_KAHAN | DC_RELU))
-    return dc::fail(DC_ERR_ARG, "dc_batch_create: flags may be DC_KAHAN | DC_RELU");
+  if (flags & ~(DC_KAHAN | DC_RELU | DC_PERSISTENT_FILTER))
+    return dc::fail(DC_ERR_ARG,
+                    "dc_batch_create: flags may be DC_KAHAN | DC_RELU | DC_PERSISTENT_FILTER");
   if (!encode_fn()) return dc::fail(DC_ERR_UNSUPPORTED, "dc_batch_create: no TMA encoder");
   int dev = -1;
   cudaGetDevice(&dev);
@@ -1298,13 +1300,15 @@ int dc_batch_create(int n, dc_geometry *const *geoms, int dtype, unsigned flags,
   if (e != cudaSuccess) return bail(dc::cuda_fail(e, "dc_batch_create: tables"));
   int rc = build_batch_tables(b);
   if (rc) return bail(rc);
-  // one persistent launch filters every problem; problems whose rows do not
-  // fit its shared memory keep the per-problem filter calls
-  rc = dc::batch_filter_create(n, b->geoms, dtype, b->gF, b->scale, &b->fplan);
-  if (rc == DC_ERR_UNSUPPORTED) {
-    b->fplan = nullptr;
-  } else if (rc) {
-    return bail(rc);
+  // optionally one persistent launch filters every problem; problems whose
+  // rows do not fit its shared memory keep the per-problem filter calls
+  if (flags & DC_PERSISTENT_FILTER) {
+    rc = dc::batch_filter_create(n, b->geoms, dtype, b->gF, b->scale, &b->fplan);
+    if (rc == DC_ERR_UNSUPPORTED) {
+      b->fplan = nullptr;
+    } else if (rc) {
+      return bail(rc);
+    }
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

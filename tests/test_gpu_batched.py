@@ -1,7 +1,7 @@
 """Batched reconstruction (one persistent backprojection over uneven
-problems) and its CUDA-graph capture: every volume against the FP64 oracle's
-reconstruction of its own problem (Eq. 12), and against the per-problem
-calls."""
+problems, their filters either chunked or in one persistent launch) and its
+CUDA-graph capture: every volume against the FP64 oracle's reconstruction of
+its own problem (Eq. 12), and against the per-problem calls."""
 import numpy as np
 import pytest
 import torch
@@ -28,8 +28,9 @@ def _problems():
 
 # FP32: the method's 1e-4 target; BF16 / FP16 storage of g^F: the stated
 # storage error of those forms (measured ~7e-4 and ~1e-4 on these problems)
+@pytest.mark.parametrize("persistent", [False, True])
 @pytest.mark.parametrize("dtype,tol", [("f32", 1e-4), ("bf16", 3e-3), ("f16", 5e-4)])
-def test_batched_matches_oracle(dtype, tol):
+def test_batched_matches_oracle(dtype, tol, persistent):
     probs = _problems()
     geoms = [p[1] for p in probs]
     g_list = [p[2] for p in probs]
@@ -39,7 +40,7 @@ def test_batched_matches_oracle(dtype, tol):
     W_list = [torch.as_tensor(Wn, device="cuda") for Wn in W_np]
     # one problem keeps the default weight 1/2
     W_list[1] = None
-    batch = api.Batch(geoms, dtype=dtype, kahan=(dtype != "f32"))
+    batch = api.Batch(geoms, dtype=dtype, kahan=(dtype != "f32"), persistent_filter=persistent)
     vols = [torch.full(geom.vol_shape, float("nan"), device="cuda") for geom in geoms]
     batch.run(g_list, vols, W_list)
     torch.cuda.synchronize()
@@ -65,7 +66,7 @@ def test_batched_equals_per_problem_calls(dtype, tol):
     probs = _problems()
     geoms = [p[1] for p in probs]
     g_list = [p[2] for p in probs]
-    batch = api.Batch(geoms, dtype=dtype, kahan=(dtype != "f32"))
+    batch = api.Batch(geoms, dtype=dtype, kahan=(dtype != "f32"), persistent_filter=True)
     vols = [torch.full(geom.vol_shape, float("nan"), device="cuda") for geom in geoms]
     batch.run(g_list, vols)
     for (w, geom, g), v in zip(probs, vols):
@@ -84,7 +85,7 @@ def test_batched_graph_replay_and_weights():
     geoms = [p[1] for p in probs]
     g_list = [p[2] for p in probs]
     W_list = [torch.rand((geom.V,) + geom.sino_shape, device="cuda") for geom in geoms]
-    batch = api.Batch(geoms)
+    batch = api.Batch(geoms, persistent_filter=True)
     tuned = tune.autotune_batch(batch, g_list, [torch.empty(gm.vol_shape, device="cuda")
                                                 for gm in geoms])
     assert tuned["bp_nz"] in (0, 16, 32)   # 0: each problem's own depth
