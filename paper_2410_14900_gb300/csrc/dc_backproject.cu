@@ -699,6 +699,7 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_batched(const BatchPro
 // voxel's distance is at least d_min.  That bound maps to 2^30, so the sums
 // cannot overflow; each contribution is rounded to the nearest unit.
 constexpr int TA_S = TB_BWW + 1;
+static_assert(TB_NZ == 32, "the adjoint rotates each lane's voxel order by its lane index");
 static_assert(TB_BWW == 64 && TB_BWN == 32,
               "the tile flush and the pair copy index columns with shifts");
 
@@ -731,11 +732,20 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
   const size_t np = (size_t)a.H * a.W;
   const size_t nvox = (size_t)a.nx * a.ny * a.nz;
   const bool inside = (ix < a.nx && iy < a.ny);
+  // Lane l takes its column's voxels in the rotated order kz = (k + l) mod
+  // TB_NZ, so that at each step the lanes of a warp are at different depths
+  // along z: lanes whose columns project to the same detector column (the
+  // columns of a warp lined up with the view direction) then hit different
+  // detector rows, and the row stride of the tile (TA_S) spreads those rows
+  // over the banks.  The fixed-point sums are exact, so the order does not
+  // change the result.  gv[k] holds voxel kz.
+  const int rot = tid & 31;
+  const float rotf = (float)rot;
   float gv[TB_NZ];
   float gs = 0.0f;
 #pragma unroll
   for (int k = 0; k < TB_NZ; ++k) {
-    int iz = z0 + k;
+    int iz = z0 + ((k + rot) & (TB_NZ - 1));
     gv[k] = 0.0f;
     if (inside && iz < a.nz) {
       size_t o = (size_t)b * nvox + ((size_t)iz * a.ny + iy) * a.nx + ix;
@@ -823,7 +833,8 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
 #pragma unroll
           for (int k = 0; k < TB_NZ; ++k) {
             if (gv[k] == 0.0f) continue;
-            float kf = (float)k;
+            float kf = rotf + (float)k;  // voxel (k + rot) mod TB_NZ
+            kf = (kf >= (float)TB_NZ) ? kf - (float)TB_NZ : kf;
             float rw = dc::rcp_approx(fmaf(kf, dW, W0));
             float u = fminf(fmaxf(fmaf(fmaf(kf, dU, U0), rw, cul), 0.0f), umx);
             float v = fminf(fmaxf(fmaf(fmaf(kf, dV, V0), rw, cvl), 0.0f), vmx);
@@ -857,7 +868,8 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
 #pragma unroll
         for (int k = 0; k < TB_NZ; ++k) {
           if (gv[k] == 0.0f) continue;
-          float kf = (float)k;
+          float kf = rotf + (float)k;  // voxel (k + rot) mod TB_NZ
+          kf = (kf >= (float)TB_NZ) ? kf - (float)TB_NZ : kf;
           float dep = fmaf(kf, dW, W0);
           if (!(dep > 0.0f)) continue;
           float rw = __frcp_rn(dep);

@@ -616,13 +616,14 @@ __device__ __forceinline__ bool bp2d_tile(const BP2Args &a, int n, int slot, int
       } else {
         // two-tap paths (ds >= pitch, so winv >= 1): the hat weights
         // 1 - f winv and 1 - (1 - f) winv never exceed 1, so clamping them
-        // below at 0 is a saturation to [0, 1]
-        const float2 Bc2 = make_float2(M.Bc, M.Bc);
-#pragma unroll
-        for (int ry = 0; ry < RY; ++ry) {
-          const float rt = fmaf(rlf[ry], M.Bs, M.F00);
-          float2 x = __ffma2_rn(jl2, Bc2, make_float2(rt, rt));
-          if (!M.fast)
+        // below at 0 is a saturation to [0, 1].  The s-bin position of a
+        // pixel is (jl Bc + F00) + rl Bs: the first part once per angle, one
+        // packed FMA per row.
+        const float2 base = __ffma2_rn(jl2, make_float2(M.Bc, M.Bc), make_float2(M.F00, M.F00));
+        const float2 Bs2 = make_float2(M.Bs, M.Bs);
+        auto pair_row = [&](int ry, bool clamp) {
+          float2 x = __ffma2_rn(make_float2(rlf[ry], rlf[ry]), Bs2, base);
+          if (clamp)
             x = make_float2(fminf(fmaxf(x.x, M.lo), M.hi), fminf(fmaxf(x.y, M.lo), M.hi));
           // exact floor (rounded-down bits) and fraction, as in band_sum
           const float2 t = __fadd2_rd(x, M2);
@@ -637,6 +638,13 @@ __device__ __forceinline__ bool bp2d_tile(const BP2Args &a, int n, int slot, int
           const float2 w1 = make_float2(__saturatef(fmaf(f.x, M.winv, M.w1c)),
                                         __saturatef(fmaf(f.y, M.winv, M.w1c)));
           acc[ry] = __ffma2_rn(w0, p0, __ffma2_rn(w1, p1, acc[ry]));
+        };
+        if (M.fast) {
+#pragma unroll
+          for (int ry = 0; ry < RY; ++ry) pair_row(ry, false);
+        } else {
+#pragma unroll
+          for (int ry = 0; ry < RY; ++ry) pair_row(ry, true);
         }
       }
     }
