@@ -145,7 +145,8 @@ __device__ __forceinline__ float band_sum(const char *sb, unsigned cb, int nr, f
                                           float dxi) {
   const float M = 12582912.0f;  // 1.5 * 2^23: x + M rounded down holds floor(x)
   constexpr int SQ = RB + 1;
-  float sum = 0.0f;
+  // even and odd steps in two sums: half the length of the dependent chain
+  float sum[2] = {0.0f, 0.0f};
 #pragma unroll
   for (int q = 0; q < (NR ? NR : RB); ++q) {
     if (!NR && q >= nr) break;
@@ -155,9 +156,9 @@ __device__ __forceinline__ float band_sum(const char *sb, unsigned cb, int nr, f
     const unsigned off = __float_as_uint(t) * (unsigned)(SQ * 4) + cb + 4u * q;
     const float g0 = *reinterpret_cast<const float *>(sb + off);
     const float g1 = *reinterpret_cast<const float *>(sb + off + SQ * 4);
-    sum += fmaf(f, g1 - g0, g0);
+    sum[q & 1] += fmaf(f, g1 - g0, g0);
   }
-  return sum;
+  return sum[0] + sum[1];
 }
 
 // The line sums of angle group `gi` of image n (view a.v0 + n / a.B, item
