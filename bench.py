@@ -38,16 +38,35 @@ ORACLE_SAMPLE_VOXELS = 20000
 UNIT = "ms/volume"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
-# FP32 operations the algorithm needs per unit of work (FMA = 2), used for
-# the ALU roofline of the gather kernels (derivation in the design notes):
-#   k_bp3d    per voxel-view update: depth FMA, reciprocal, 2 FMA for (u,v),
-#             2 fraction subtractions, 3 lerps (sub+FMA), distance FMA x2,
-#             reciprocal, weight multiply, accumulate                   -> 25
+# FP32 operations the algorithm needs per unit of work (FMA = 2, a floor or
+# a reciprocal = 1), used for the ALU roofline of the gather kernels:
+#   k_bp3d    per voxel-view update, with the projected row differences
+#             (g[r][j+1] - g[r][j]) stored beside the values:
+#             a view whose u and depth are constant along a z column (a
+#             circle about z): v FMA (2), floor + fraction (2), two row
+#             lerps (FMA each, 4), lerp across rows (sub + FMA, 3), distance
+#             weight (2 FMA, reciprocal, multiply: 6), accumulate (1) -> 18;
+#             any other view adds depth FMA + reciprocal (3), u (2 FMA, 4),
+#             v's perspective FMA (2), floor + fraction of u (2)      -> 29;
+#             the unit count is weighted by the workload's mix of views
 #   k_linesum per Joseph step: position FMA, fraction, lerp (sub+FMA),
 #             accumulate                                                -> 7
 #   k_bp2d    per pixel-angle pair: position FMA, fraction, two hat
 #             weights (FMA+max each), two taps (FMA each)               -> 13
-FLOPS_PER_UNIT = {"k_bp3d": 25.0, "k_linesum": 7.0, "k_bp2d": 13.0}
+FLOPS_PER_UNIT = {"k_bp3d": None, "k_linesum": 7.0, "k_bp2d": 13.0}
+BP_FLOPS_COLUMN_VIEW, BP_FLOPS_GENERAL_VIEW = 18.0, 29.0
+
+
+def bp_flops_per_update(geom) -> tuple:
+    """FP32 operations per voxel-view update of the backprojection for this
+    geometry's mix of views (see FLOPS_PER_UNIT), and the fraction of views
+    whose u and depth are constant along a z column (the backprojector's own
+    test: the FP32 z-components of the l_x and l_z rows are zero)."""
+    from paper_2410_14900_gb300 import api
+    v = api.dc_get_view_geometry(geom)
+    col = (np.float32(v[:, 5]) == 0) & (np.float32(v[:, 11]) == 0)
+    frac = float(np.mean(col))
+    return BP_FLOPS_COLUMN_VIEW * frac + BP_FLOPS_GENERAL_VIEW * (1.0 - frac), frac
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -625,16 +644,19 @@ def run_ours(args, rank, world, local_rank):
     fp32_peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
     roof = None
-    if dom in FLOPS_PER_UNIT:
+    flops_unit = dict(FLOPS_PER_UNIT)
+    flops_unit["k_bp3d"], column_view_frac = bp_flops_per_update(geom)
+    if dom in flops_unit:
         per_launch_units = units[dom] * args.steps / kernels[dom]["launches"]
-        ach = per_launch_units * FLOPS_PER_UNIT[dom] / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e12
+        ach = per_launch_units * flops_unit[dom] / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak_tflops,
                 "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops,
                 "traffic": recorded_traffic(dom, per_launch_units),
                 "peak_source": f"FP32 issue rate: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x "
                                f"2 x {sm_max:.0f} MHz (max clock of {peak_kind} peaks)",
                 "units_per_launch": per_launch_units,
-                "flops_per_unit": FLOPS_PER_UNIT[dom]}
+                "flops_per_unit": flops_unit[dom],
+                "column_view_fraction": column_view_frac if dom == "k_bp3d" else None}
     filter_ms = sum(kernels.get(k, {}).get("ms_total", 0.0)
                     for k in ("k_prep", "k_linesum", "k_bp2d", "k_to_f16")) / args.steps
     bp_ms = kernels.get("k_bp3d", {}).get("ms_total", 0.0) / args.steps

@@ -708,6 +708,7 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
   __shared__ dc::BPView sv[TB_VCH];
   __shared__ int4 vtab[TB_VCH];
   __shared__ float wsum[TB_TX * TB_TY / 32];
+  __shared__ float wmax[TB_TX * TB_TY / 32];
   const int tid = threadIdx.y * TB_TX + threadIdx.x;
   const int ix = blockIdx.x * TB_TX + threadIdx.x;
   const int iy = blockIdx.y * TB_TY + threadIdx.y;
@@ -742,7 +743,7 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
   const int rot = tid & 31;
   const float rotf = (float)rot;
   float gv[TB_NZ];
-  float gs = 0.0f;
+  float gs = 0.0f, gm = 0.0f;
 #pragma unroll
   for (int k = 0; k < TB_NZ; ++k) {
     int iz = z0 + ((k + rot) & (TB_NZ - 1));
@@ -753,17 +754,34 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
       if (a.relu_vol && !(a.relu_vol[o] > 0.0f)) g = 0.0f;
       gv[k] = g;
       gs += fabsf(g);
+      gm = fmaxf(gm, fabsf(g));
     }
   }
   const bool any = gs > 0.0f;
-  for (int o = 16; o > 0; o >>= 1) gs += __shfl_xor_sync(0xffffffffu, gs, o);
-  if ((tid & 31) == 0) wsum[tid >> 5] = gs;
+  for (int o = 16; o > 0; o >>= 1) {
+    gs += __shfl_xor_sync(0xffffffffu, gs, o);
+    gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+  }
+  if ((tid & 31) == 0) {
+    wsum[tid >> 5] = gs;
+    wmax[tid >> 5] = gm;
+  }
   for (int e = tid; e < TB_BH * TA_S; e += TB_TX * TB_TY) tile[e] = 0;
   __syncthreads();
-  float gsum = 0.0f;
-  for (int q = 0; q < TB_TX * TB_TY / 32; ++q) gsum += wsum[q];
+  float gsum = 0.0f, gmax = 0.0f;
+  for (int q = 0; q < TB_TX * TB_TY / 32; ++q) {
+    gsum += wsum[q];
+    gmax = fmaxf(gmax, wmax[q]);
+  }
   gsum *= 1.0001f;  // headroom for the rounding of this sum
   if (!(gsum > 0.0f)) return;  // nothing to scatter from this box (CTA-uniform)
+  // One contribution is at most gmax / d^2 <= gmax / dmin^2, i.e. at most
+  // 2^30 gmax / gsum units.  When the box's gradient is spread over at least
+  // 512 voxels' worth of its largest value, every contribution stays below
+  // 2^21 units and is rounded to an integer by adding 1.5 * 2^23 (the sum
+  // has unit spacing, and round-to-nearest-even is the same rounding as
+  // __float2int_rn) instead of a conversion instruction.  CTA-uniform.
+  const bool magic_round = gsum >= 512.0f * gmax;
   float *gbase = a.grad_gF + (size_t)b * a.V * np;
 
   for (int c0 = 0; c0 < a.V; c0 += TB_VCH) {
@@ -829,7 +847,7 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
         const float from_fix = bound * (1.0f / 1073741824.0f);
         const float cul = w.pp.x - (float)t.x, cvl = w.pp.y - (float)t.y;
         const float umx = (float)TB_BWW - 1.001f, vmx = (float)TB_BH - 1.001f;
-        if (any) {
+        auto scatter = [&](auto to_int) {
 #pragma unroll
           for (int k = 0; k < TB_NZ; ++k) {
             if (gv[k] == 0.0f) continue;
@@ -845,11 +863,19 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
             int *p = tile + r * TA_S + j;
             float g1 = gk * fv, g0 = gk - g1;
             float g01 = g0 * fu, g11 = g1 * fu;
-            atomicAdd(p, __float2int_rn(g0 - g01));
-            atomicAdd(p + 1, __float2int_rn(g01));
-            atomicAdd(p + TA_S, __float2int_rn(g1 - g11));
-            atomicAdd(p + TA_S + 1, __float2int_rn(g11));
+            atomicAdd(p, to_int(g0 - g01));
+            atomicAdd(p + 1, to_int(g01));
+            atomicAdd(p + TA_S, to_int(g1 - g11));
+            atomicAdd(p + TA_S + 1, to_int(g11));
           }
+        };
+        if (any) {
+          if (magic_round)
+            scatter([](float x) {
+              return __float_as_int(__fadd_rn(x, 12582912.0f)) - 0x4B400000;  // |x| < 2^22
+            });
+          else
+            scatter([](float x) { return __float2int_rn(x); });
         }
         __syncthreads();
         // flush the whole tile (pixels inside the detector) and clear it
