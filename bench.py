@@ -181,7 +181,9 @@ def work_units(desc, B):
     """Algorithmic units per step: Joseph steps, pixel-angle pairs, updates."""
     V, H, W = desc["n_views"], desc["det_rows"], desc["det_cols"]
     n_mu, n_s = desc["n_mu"], desc["n_s"]
-    rows = sum(H if (4 * m <= n_mu or 4 * m >= 3 * n_mu) else W for m in range(n_mu))
+    # steps per line: detector rows for the row-stepping angles (the same
+    # integer test as the library: 4m < n_mu or 4m >= 3 n_mu), columns else
+    rows = sum(H if (4 * m < n_mu or 4 * m >= 3 * n_mu) else W for m in range(n_mu))
     return {"k_linesum": float(B) * V * rows * n_s,
             "k_bp2d": float(B) * V * n_mu * H * W,
             "k_bp3d": float(B) * V * desc["vol_x"] * desc["vol_y"] * desc["vol_z"]}

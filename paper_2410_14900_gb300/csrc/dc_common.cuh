@@ -199,12 +199,20 @@ inline __host__ __device__ float split_hi12(double v) {
   return (float)(rint(v * 4096.0) / 4096.0);
 }
 
-// The per-angle record of angle m = mu_m / (pi / n_mu), from FP64 (host or
-// device).  The Joseph branch is decided exactly: 4m <= n_mu or 4m >= 3 n_mu
-// steps over rows (|cos| >= |sin|, ties included).
+// The Joseph branch of angle m = mu_m / (pi / n_mu), decided exactly by
+// integers: rows (|cos| > |sin|) when 4m < n_mu or 4m >= 3 n_mu.  Of the two
+// 45-degree ties, mu = pi/4 steps over columns and mu = 3pi/4 over rows, so
+// that each branch has n_mu / 2 angles when 4 divides n_mu (equal angle
+// groups for the line sums); on a line of slope +-1 both branches sample the
+// same points with the same weights, so the tie may go either way.
+inline __host__ __device__ bool joseph_rows(int m, int n_mu) {
+  return (4 * m < n_mu) || (4 * m >= 3 * n_mu);
+}
+
+// The per-angle record of angle m, from FP64 (host or device).
 inline __host__ __device__ MuRec make_mu_rec(int m, int n_mu, double pitch, double ds) {
   double ang = m * 3.14159265358979323846 / n_mu, c = cos(ang), s = sin(ang);
-  bool rows = (4 * m <= n_mu) || (4 * m >= 3 * n_mu);
+  bool rows = joseph_rows(m, n_mu);
   double cs = rows ? c : s, sn = rows ? s : c;
   double mx = fabs(cs);
   MuRec r;
@@ -230,7 +238,7 @@ inline __host__ __device__ MuRec make_mu_rec(int m, int n_mu, double pitch, doub
 inline __host__ __device__ VMu make_vmu(int m, int n_mu, int n_s, double pitch, double ds,
                                         double cu, double cv) {
   double ang = m * 3.14159265358979323846 / n_mu, c = cos(ang), s = sin(ang);
-  bool rows = (4 * m <= n_mu) || (4 * m >= 3 * n_mu);
+  bool rows = joseph_rows(m, n_mu);
   double cs = rows ? c : s, sn = rows ? s : c;
   double ccol = rows ? cu : cv, crow = rows ? cv : cu;
   double b0 = ccol + crow * sn / cs;

@@ -1701,7 +1701,7 @@ __global__ void k_na_tables(int n_mu, int n_s, double pitch, double ds, double c
   for (int br = 0; br < 2; ++br) {
     int cnt = 0;
     for (int q = 0; q < n_mu; ++q) {
-      bool rows = (4 * q <= n_mu) || (4 * q >= 3 * n_mu);
+      bool rows = dc::joseph_rows(q, n_mu);
       if ((br == 0) != rows) continue;
       if (cnt % mg == 0) {
         groups[ng].first = nord;
@@ -1781,7 +1781,7 @@ extern "C" int dc_radon2d_noalloc(int n_img, int H, int W, int n_mu, int n_s, do
   DC_CHECK_LAUNCH("k_na_tables");
   // the group count is a host-side launch parameter: recompute it here
   int nb0 = 0, nb1 = 0;
-  for (int m = 0; m < n_mu; ++m) ((4 * m <= n_mu) || (4 * m >= 3 * n_mu) ? nb0 : nb1) += 1;
+  for (int m = 0; m < n_mu; ++m) (dc::joseph_rows(m, n_mu) ? nb0 : nb1) += 1;
   const int n_groups_h = (nb0 + mg - 1) / mg + (nb1 + mg - 1) / mg;
 
   const int per_chunk = (int)std::min<size_t>(cap / per_img, 65535);

@@ -179,16 +179,15 @@ void free_geometry(dc_geometry *g) {
 namespace dc {
 
 // Angle tables: cos/sin in FP64 -> FP32, the Joseph branch decided exactly by
-// the integer test 4m <= n_mu or 4m >= 3 n_mu (|cos| >= |sin|, ties to the
-// row-stepping branch), and groups of angles of one branch for the line-sum
-// kernel.
+// an integer test (joseph_rows), and groups of angles of one branch for the
+// line-sum kernel.
 int build_mu_tables(dc_geometry *g) {
   const dc_geometry_desc &d = g->d;
   int n_mu = d.n_mu;
   std::vector<MuRec> mu(n_mu);
   std::vector<int> b0, b1;
   for (int m = 0; m < n_mu; ++m) {
-    bool rows = (4 * m <= n_mu) || (4 * m >= 3 * n_mu);
+    bool rows = joseph_rows(m, n_mu);
     mu[m] = make_mu_rec(m, n_mu, d.pitch, d.ds);
     (rows ? b0 : b1).push_back(m);
   }
