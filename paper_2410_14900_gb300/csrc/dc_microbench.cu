@@ -6,7 +6,8 @@
 //           fraction, two taps of a [sample][33] band, linear interpolation,
 //           accumulate; neighbouring lanes ~1.2 samples apart
 //   kind 1  transposed-hat pair (k_bp2d): affine position, two taps of a row,
-//           two clamped hat weights, accumulate
+//           two saturated hat weights, accumulate; two pixels per thread in
+//           packed FP32x2 operations
 //   kind 2  bilinear sample (k_bp3d_tma): affine position in v with a fixed
 //           column, exact floor and fraction, two (value, difference) pairs,
 //           three interpolations, accumulate
@@ -57,22 +58,32 @@ __global__ void __launch_bounds__(MB_THREADS) k_microbench(int kind, int iters, 
       }
     }
   } else if (kind == 1) {
+    // two pixels (columns lane, lane + 32) per thread in packed FP32x2, as in
+    // k_bp2d; s-bin positions stay below 80 of the 520-float rows
     const float Bc = 0.83f, winv = 1.21f, w1c = 1.0f - 1.21f;
+    const float2 M2 = make_float2(M, M), mM2 = make_float2(-M, -M), m12 = make_float2(-1.f, -1.f);
+    float2 a2 = make_float2(0.0f, 0.0f);
     for (int it = 0; it < iters; ++it) {
       const float rt = 3.0f + 0.5f * (float)warp + 0.001f * (float)(it & 7);
       const unsigned cb = (unsigned)((it & 7) * 520 * 4) - 4u * 0x4B400000u;
+      const float2 base = __ffma2_rn(make_float2((float)lane, (float)(lane + 32)),
+                                     make_float2(Bc, Bc), make_float2(rt, rt));
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const float x = fmaf((float)(lane + 32 * (q & 1)), Bc, rt + (float)(q >> 1));
-        const float t = __fadd_rd(x, M);
-        const unsigned off = __float_as_uint(t) * 4u + cb;
-        const float p0 = ldf(sb, off), p1 = ldf(sb, off + 4);
-        const float f = x - (t - M);
-        const float w0 = fmaxf(0.0f, fmaf(-f, winv, 1.0f));
-        const float w1 = fmaxf(0.0f, fmaf(f, winv, w1c));
-        acc = fmaf(w0, p0, fmaf(w1, p1, acc));
+      for (int q = 0; q < 16; ++q) {
+        const float2 x = __fadd2_rn(base, make_float2((float)q, (float)q));
+        const float2 t = __fadd2_rd(x, M2);
+        const float2 f = __ffma2_rn(__fadd2_rn(t, mM2), m12, x);
+        const unsigned o0 = __float_as_uint(t.x) * 4u + cb, o1 = __float_as_uint(t.y) * 4u + cb;
+        const float2 p0 = make_float2(ldf(sb, o0), ldf(sb, o1));
+        const float2 p1 = make_float2(ldf(sb, o0 + 4), ldf(sb, o1 + 4));
+        const float2 w0 = make_float2(__saturatef(fmaf(-f.x, winv, 1.0f)),
+                                      __saturatef(fmaf(-f.y, winv, 1.0f)));
+        const float2 w1 = make_float2(__saturatef(fmaf(f.x, winv, w1c)),
+                                      __saturatef(fmaf(f.y, winv, w1c)));
+        a2 = __ffma2_rn(w0, p0, __ffma2_rn(w1, p1, a2));
       }
     }
+    acc = a2.x + a2.y;
   } else {
     // pair tile of 40 rows x 72 float2 (row stride 576 bytes)
     const float fu = 0.3f + 0.01f * (float)lane;
