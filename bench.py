@@ -90,7 +90,40 @@ def parse():
                     help="only the batched-orbits measurement (for profiling)")
     ap.add_argument("--train-only", action="store_true",
                     help="only the training-step measurement (for profiling)")
+    ap.add_argument("--profile-case", choices=["filter_bp", "adj"], default=None,
+                    help="run one small case twice for an ncu capture and exit: filter_bp = "
+                         "the headline orbit, detector and planes with a 256^3 volume at the "
+                         "headline voxel size (19 images per filter chunk); adj = the "
+                         "backprojection transpose on the 256^3 sinusoid training geometry "
+                         "with 90 views, batch 1")
     return ap.parse_args()
+
+
+def profile_case(case: str, dev):
+    """Small cases whose kernels are those of the full workloads, for ncu
+    captures that end quickly (inputs still larger than L2)."""
+    import torch
+    from paper_2410_14900_gb300 import api, synth
+    if case == "filter_bp":
+        w = synth.workload("circle_arc512")
+        desc = w.desc_dict()
+        desc.update(vol_x=256, vol_y=256, vol_z=256)
+        geom = api.Geometry(desc, w.matrices(), w.orbit.vdl)
+        api.dc_geometry_set_tuning(geom, 19, 32)
+        g = torch.randn((1, w.n_views, w.det_rows, w.det_cols), device=dev)
+        for _ in range(2):
+            gF, _ = api.dc_filter(geom, g)
+            api.dc_backproject(geom, gF)
+    else:
+        w = synth.scaled_workload("sinusoid256_train", views=90)
+        geom = api.Geometry(w.desc_dict(), w.matrices(), w.orbit.vdl)
+        gv = torch.randn((1,) + geom.vol_shape, device=dev)
+        for _ in range(2):
+            api.dc_backproject_adjoint(geom, gv)
+    torch.cuda.synchronize()
+    api.dc_sync_status(geom)
+    geom.close()
+    print(json.dumps({"profile_case": case, "ok": True}), flush=True)
 
 
 # --------------------------------------------------------------- utilities
@@ -799,6 +832,11 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.profile_case:
+        import torch
+        torch.cuda.set_device(local_rank)
+        profile_case(args.profile_case, torch.device("cuda", local_rank))
         return
     if args.batched_only:
         import torch
