@@ -6,7 +6,10 @@ then dc_backproject.  Default workload: circle (360 views) plus a
 perpendicular 60-degree arc (136 views), 384x512 detector at 0.6 mm,
 720 x 512 planes per view, 512^3 volume, FP32 (the circle-plus-arc
 configuration of the paper's workload class), seeded 20-ellipsoid phantom
-with exact line integrals.
+with exact line integrals.  g^F is stored as FP32 (value, right difference)
+pairs by default (--storage f32x2: the FP32 values and their FP32
+differences, which the backprojection reads as its interpolation tiles);
+--storage f32 / bf16 / f16 time the other forms.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -78,7 +81,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="circle_arc512")
-    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--storage", default="f32x2", choices=["f32", "f32x2", "bf16", "f16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
@@ -99,7 +102,7 @@ def parse():
     return ap.parse_args()
 
 
-def profile_case(case: str, dev):
+def profile_case(case: str, dev, storage: str = "f32"):
     """Small cases whose kernels are those of the full workloads, for ncu
     captures that end quickly (inputs still larger than L2)."""
     import torch
@@ -112,7 +115,7 @@ def profile_case(case: str, dev):
         api.dc_geometry_set_tuning(geom, 19, 32)
         g = torch.randn((1, w.n_views, w.det_rows, w.det_cols), device=dev)
         for _ in range(2):
-            gF, _ = api.dc_filter(geom, g)
+            gF, _ = api.dc_filter(geom, g, None, storage)
             api.dc_backproject(geom, gF)
     else:
         w = synth.scaled_workload("sinusoid256_train", views=90)
@@ -618,12 +621,11 @@ def run_ours(args, rank, world, local_rank):
                               device=dev, dtype=torch.float32)[None].contiguous()
     B = 1
     V, H, Wd = w.n_views, w.det_rows, w.det_cols
-    gF = torch.empty((B, V, H, Wd), device=dev,
-                     dtype={"f32": torch.float32, "bf16": torch.bfloat16,
-                            "f16": torch.float16}[args.storage])
+    gF = torch.empty(api.gF_shape(geom, B, args.storage), device=dev,
+                     dtype=api._DTYPES[args.storage][1])
     scale = torch.empty((B, V), device=dev) if args.storage == "f16" else None
     vol = torch.empty((B,) + geom.vol_shape, device=dev)
-    kahan = args.storage != "f32"
+    kahan = args.storage in ("bf16", "f16")
 
     def step():
         api.dc_filter(geom, g, None, args.storage, out=gF, scale=scale)
@@ -693,10 +695,10 @@ def run_ours(args, rank, world, local_rank):
                 "flops_per_unit": flops_unit[dom],
                 "column_view_fraction": column_view_frac if dom == "k_bp3d" else None}
     filter_ms = sum(kernels.get(k, {}).get("ms_total", 0.0)
-                    for k in ("k_prep", "k_linesum", "k_bp2d", "k_to_f16")) / args.steps
+                    for k in ("k_prep", "k_linesum", "k_bp2d", "k_to_f16", "k_to_pairs")) / args.steps
     bp_ms = kernels.get("k_bp3d", {}).get("ms_total", 0.0) / args.steps
     hbm_bytes = (B * V * H * Wd * 4  # read g
-                 + 2 * B * V * H * Wd * gF.element_size()  # write + read g^F
+                 + 2 * gF.numel() * gF.element_size()  # write + read g^F
                  + vol.numel() * 4)  # write f
     if interp:
         # each kernel's own rate (work units per second of its launches) as
@@ -754,33 +756,39 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": int(g.numel() * 4), "d2h_bytes_per_step": int(vol.numel() * 4),
                "api": "dc_reconstruct_host (transfers overlapped with the kernels)"}
 
-    # the chosen low-precision form next to the plain FP32 path
+    # the other storage forms of g^F next to the timed one: FP32, FP32 pairs
+    # (the same values; the backprojection reads its tiles in place), BF16 /
+    # FP16 with Kahan summation
     forms = None
-    if not args.no_forms and args.storage == "f32":
-        forms = {"f32_gF_bytes_per_volume": int(gF.numel() * gF.element_size())}
-        for st in ("bf16", "f16"):
-            # voxels per thread along z tuned for this storage form with Kahan
-            ft = tune.autotune(geom, st, chunks=(tuned["chunk_images"],), nzs=(16, 32), kahan=True)
+    if not args.no_forms and args.storage in ("f32", "f32x2"):
+        forms = {f"{args.storage}_gF_bytes_per_volume": int(gF.numel() * gF.element_size())}
+        for st in ("f32", "f32x2", "bf16", "f16"):
+            if st == args.storage:
+                continue
+            kh = st in ("bf16", "f16")
+            # voxels per thread along z tuned for this storage form
+            ft = tune.autotune(geom, st, chunks=(tuned["chunk_images"],), nzs=(16, 32), kahan=kh)
             forms[f"{st}_bp_nz"] = ft["bp_nz"]
-            gF2 = torch.empty((B, V, H, Wd), device=dev,
-                              dtype=torch.bfloat16 if st == "bf16" else torch.float16)
+            gF2 = torch.empty(api.gF_shape(geom, B, st), device=dev, dtype=api._DTYPES[st][1])
             sc2 = torch.empty((B, V), device=dev) if st == "f16" else None
             for _ in range(2):
                 api.dc_filter(geom, g, None, st, out=gF2, scale=sc2)
-                api.dc_backproject(geom, gF2, sc2, out=vol, kahan=True)
+                api.dc_backproject(geom, gF2, sc2, out=vol, kahan=kh)
             torch.cuda.synchronize()
             f0 = torch.cuda.Event(enable_timing=True)
             f1 = torch.cuda.Event(enable_timing=True)
             f0.record(stream)
             for _ in range(args.steps):
                 api.dc_filter(geom, g, None, st, out=gF2, scale=sc2)
-                api.dc_backproject(geom, gF2, sc2, out=vol, kahan=True)
+                api.dc_backproject(geom, gF2, sc2, out=vol, kahan=kh)
             f1.record(stream)
             torch.cuda.synchronize()
-            forms[f"{st}_storage_kahan_ms_per_volume"] = f0.elapsed_time(f1) / args.steps
+            key = f"{st}_storage_kahan_ms_per_volume" if kh else f"{st}_storage_ms_per_volume"
+            forms[key] = f0.elapsed_time(f1) / args.steps
             forms[f"{st}_gF_bytes_per_volume"] = int(gF2.numel() * gF2.element_size()
                                                      + (sc2.numel() * 4 if sc2 is not None else 0))
             del gF2
+        api.dc_geometry_set_tuning(geom, tuned["chunk_images"], tuned["bp_nz"])
 
     batched = None
     if not args.no_batched:
@@ -836,7 +844,7 @@ def main():
     if args.profile_case:
         import torch
         torch.cuda.set_device(local_rank)
-        profile_case(args.profile_case, torch.device("cuda", local_rank))
+        profile_case(args.profile_case, torch.device("cuda", local_rank), args.storage)
         return
     if args.batched_only:
         import torch

@@ -64,6 +64,12 @@ extern "C" {
 #define DC_F32 0
 #define DC_BF16 1             /* round-to-nearest-even                      */
 #define DC_F16 2              /* with a per-view power-of-two scale         */
+/* FP32 (value, right difference) pairs: pixel (r, c) of g^F is stored as
+ * the two floats g[r][c] and g[r][c+1] - g[r][c] (g[r][W] = 0), i.e.
+ * [B][V][H][W][2] FP32, 16-byte aligned.  The same values as DC_F32 at twice
+ * the bytes; the backprojection reads its interpolation tiles in place
+ * instead of building them. */
+#define DC_F32X2 3
 
 /* dc_backproject flags */
 #define DC_ACCUM 1u           /* add into vol instead of overwriting        */
@@ -139,7 +145,7 @@ int dc_get_view_geometry(const dc_geometry *geom, double *out);
  *   W       : device, [V][n_mu][n_s] FP32 redundancy weights, or NULL for
  *             the constant 1/2 (exact for a full circle, Eq. 14).
  *   gF      : device, [B][V][H][W] output in `dtype` (DC_F32, DC_BF16,
- *             DC_F16).
+ *             DC_F16), or [B][V][H][W][2] FP32 for DC_F32X2 (16-byte aligned).
  *   gF_scale: device, [B][V] FP32, required for DC_F16 (g^F = half * scale),
  *             ignored otherwise.
  * Requires ds >= pitch / 3 (below pitch a pixel meets up to six lines).
@@ -185,7 +191,8 @@ int dc_filter_adjoint_from_s(const dc_geometry *geom, int B, const float *grad_g
  * Pixels outside the detector count as zero; voxels with depth <= 0 in a
  * view get nothing from it.  Interpolation and accumulation are FP32 for
  * every storage type.
- *   gF      : device, [B][V][H][W] in `dtype`; gF_scale [B][V] for DC_F16.
+ *   gF      : device, [B][V][H][W] in `dtype` ([B][V][H][W][2] FP32 for
+ *             DC_F32X2); gF_scale [B][V] for DC_F16.
  *   vol     : device, [B][Z][Y][X] FP32, overwritten (or added to with
  *             DC_ACCUM).
  *   flags   : DC_ACCUM | DC_KAHAN | DC_RELU.
@@ -295,7 +302,9 @@ int dc_gauss_smooth(int V, int n_mu, int n_s, float sigma, int radius, int adjoi
  * kernel runs its 2-D backprojection at half the warps per SM of the
  * chunked kernel and is ~11% slower; it is kept for launch-bound uses.)
  * With the flag, problems whose detector or sinogram rows do not fit that
- * kernel's shared memory fall back to the per-problem calls.
+ * kernel's shared memory fall back to the per-problem calls, and so does
+ * every problem of a DC_F32X2 batch (the pairs are made by the chunked
+ * filter's pass over each finished image).
  */
 typedef struct dc_batch dc_batch;
 int dc_batch_create(int n, dc_geometry *const *geoms, int dtype, unsigned flags,

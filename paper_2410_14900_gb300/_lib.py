@@ -17,7 +17,7 @@ _lib = None
 
 (DC_OK, DC_ERR_ARG, DC_ERR_CUDA, DC_ERR_OOM, DC_ERR_TIMEOUT, DC_ERR_UNSUPPORTED,
  DC_ERR_NONFINITE) = range(7)
-DC_F32, DC_BF16, DC_F16 = 0, 1, 2
+DC_F32, DC_BF16, DC_F16, DC_F32X2 = 0, 1, 2, 3
 DC_ACCUM, DC_KAHAN, DC_RELU = 1, 2, 4
 DC_PERSISTENT_FILTER = 8
 DC_VIEW_GEO_N = 24

@@ -16,11 +16,25 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (DC_ACCUM, DC_BF16, DC_F16, DC_F32, DC_KAHAN, DC_PERSISTENT_FILTER, DC_RELU,
-                   check)
+from ._lib import (DC_ACCUM, DC_BF16, DC_F16, DC_F32, DC_F32X2, DC_KAHAN, DC_PERSISTENT_FILTER,
+                   DC_RELU, check)
 
+# storage forms of g^F: code, torch dtype; "f32x2" holds (value, right
+# difference) FP32 pairs in a trailing dimension of 2
 _DTYPES = {"f32": (DC_F32, torch.float32), "bf16": (DC_BF16, torch.bfloat16),
-           "f16": (DC_F16, torch.float16)}
+           "f16": (DC_F16, torch.float16), "f32x2": (DC_F32X2, torch.float32)}
+
+
+def gF_shape(geom: "Geometry", B: int, dtype: str = "f32") -> tuple:
+    """Shape of g^F in a storage form."""
+    shp = (B, geom.V, geom.H, geom.W)
+    return shp + (2,) if dtype == "f32x2" else shp
+
+
+def _gF_code(gF: torch.Tensor) -> int:
+    if gF.dtype == torch.float32 and gF.dim() == 5:
+        return DC_F32X2
+    return {torch.float32: DC_F32, torch.bfloat16: DC_BF16, torch.float16: DC_F16}[gF.dtype]
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -138,8 +152,8 @@ def dc_filter(geom: Geometry, g: torch.Tensor, W: Optional[torch.Tensor] = None,
         _need(W, "W", torch.float32, (geom.V,) + geom.sino_shape)
     code, tdt = _DTYPES[dtype]
     if out is None:
-        out = torch.empty((B, geom.V, geom.H, geom.W), device=g.device, dtype=tdt)
-    _need(out, "gF", tdt, (B, geom.V, geom.H, geom.W))
+        out = torch.empty(gF_shape(geom, B, dtype), device=g.device, dtype=tdt)
+    _need(out, "gF", tdt, gF_shape(geom, B, dtype))
     if code == DC_F16 and scale is None:
         scale = torch.empty((B, geom.V), device=g.device, dtype=torch.float32)
     if S_out is not None:
@@ -189,10 +203,11 @@ def dc_filter_adjoint(geom: Geometry, grad_gF: torch.Tensor, g: Optional[torch.T
 def dc_backproject(geom: Geometry, gF: torch.Tensor, scale: Optional[torch.Tensor] = None,
                    out: Optional[torch.Tensor] = None, accum: bool = False,
                    kahan: bool = False, relu: bool = False) -> torch.Tensor:
-    """f = A3d^T g^F (Eq. 5), optional ReLU; g^F in f32, bf16 or f16 (+scale)."""
+    """f = A3d^T g^F (Eq. 5), optional ReLU; g^F in f32, f32x2 ([..., 2] pairs),
+    bf16 or f16 (+scale)."""
     B = gF.shape[0]
-    code = {torch.float32: DC_F32, torch.bfloat16: DC_BF16, torch.float16: DC_F16}[gF.dtype]
-    _need(gF, "gF", gF.dtype, (B, geom.V, geom.H, geom.W))
+    code = _gF_code(gF)
+    _need(gF, "gF", gF.dtype, (B, geom.V, geom.H, geom.W) + ((2,) if code == DC_F32X2 else ()))
     if code == DC_F16:
         if scale is None:
             raise ValueError("f16 g^F needs its scale")
@@ -408,12 +423,12 @@ def dc_reconstruct_host(geom: Geometry, g_host: torch.Tensor, vol_host: torch.Te
     if W is not None:
         _need(W, "W", torch.float32, (geom.V,) + geom.sino_shape)
     g_dev = torch.empty(shp, device=device, dtype=torch.float32) if g_dev is None else g_dev
-    gF = torch.empty(shp, device=device, dtype=tdt) if gF is None else gF
+    gF = torch.empty(gF_shape(geom, B, dtype), device=device, dtype=tdt) if gF is None else gF
     vol_dev = torch.empty((B,) + geom.vol_shape, device=device) if vol_dev is None else vol_dev
     if code == DC_F16 and scale is None:
         scale = torch.empty((B, geom.V), device=device, dtype=torch.float32)
     _need(g_dev, "g_dev", torch.float32, shp)
-    _need(gF, "gF", tdt, shp)
+    _need(gF, "gF", tdt, gF_shape(geom, B, dtype))
     _need(vol_dev, "vol_dev", torch.float32, (B,) + geom.vol_shape)
     flags = (DC_KAHAN if kahan else 0) | (DC_RELU if relu else 0)
     check(_lib.load().dc_reconstruct_host(geom.handle, B, g_host.data_ptr(), _ptr(W), _ptr(g_dev),

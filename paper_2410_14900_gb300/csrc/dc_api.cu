@@ -139,7 +139,7 @@ int dc_profile_collect(double *ms, unsigned long long *launches, int n) {
 const char *dc_profile_kernel_name(int id) {
   static const char *names[] = {"k_prep", "k_linesum", "k_bp2d", "k_to_f16",
                                 "k_reduce_gradW", "k_sino_in", "k_bp3d", "k_bp3d_adj",
-                                "k_smooth", "k_adj_from_s", "k_filter_batched"};
+                                "k_smooth", "k_adj_from_s", "k_filter_batched", "k_to_pairs"};
   return (id >= 0 && id < dc::KID_COUNT) ? names[id] : "";
 }
 

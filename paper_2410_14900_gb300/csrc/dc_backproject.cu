@@ -51,6 +51,11 @@ __device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16 *p) {
 }
 template <>
 __device__ __forceinline__ float ld<__half>(const __half *p) { return __half2float(__ldg(p)); }
+// DC_F32X2: the value is the first half of the (g, right difference) pair
+template <>
+__device__ __forceinline__ float ld<float2>(const float2 *p) {
+  return __ldg(reinterpret_cast<const float *>(p));
+}
 
 // bilinear interpolation with zero outside the detector
 template <typename T>
@@ -241,6 +246,22 @@ constexpr int TB_NS = 3;
 constexpr int TB_VCH = 32;
 enum { FP_GLOBAL = 0, FP_NARROW = 1, FP_WIDE = 2, FP_SKIP = 3 };
 
+// With DC_F32X2 storage g^F already holds the (g, right difference) pairs
+// of the work tile, so the TMA box itself is the tile, read in place: boxes
+// of 40 or 72 pairs give a row stride of 8 mod 16 pairs (the bank spread of
+// the converted tile below), and every staged column is usable.
+constexpr int TB_PBWN = 40, TB_PBWW = 72;
+template <typename T>
+struct TileShape {
+  static constexpr bool PAIRS = false;
+  static constexpr int BWN = TB_BWN, BWW = TB_BWW;
+};
+template <>
+struct TileShape<float2> {
+  static constexpr bool PAIRS = true;
+  static constexpr int BWN = TB_PBWN, BWW = TB_PBWW;
+};
+
 template <typename T>
 __device__ __forceinline__ float sld(const T *p);
 template <>
@@ -256,10 +277,14 @@ __device__ __forceinline__ float sld<__half>(const __half *p) { return __half2fl
 // work tiles of tap pairs (g[r][j], g[r][j+1] - g[r][j]) with a row stride
 // of TB_S2 float2 (8 mod 16): adjacent rows put one column on different
 // banks, a row's linear interpolation is one 64-bit load and one FMA.
+// DC_F32X2 storage needs only the stages (the pairs come from g^F).
 constexpr int TB_S2 = TB_BWW + 8;
 template <typename T>
 constexpr size_t bp_tma_smem() {
-  return (size_t)TB_NS * TB_BH * TB_BWW * sizeof(T) + 2 * (size_t)TB_BH * TB_S2 * sizeof(float2);
+  return TileShape<T>::PAIRS
+             ? (size_t)TB_NS * TB_BH * TB_PBWW * sizeof(T)
+             : (size_t)TB_NS * TB_BH * TB_BWW * sizeof(T) +
+                   2 * (size_t)TB_BH * TB_S2 * sizeof(float2);
 }
 
 // Tap addressing without integer conversions: x + kM rounded toward -inf is
@@ -281,8 +306,10 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
                                        const CUtensorMap *tmw, unsigned *err, int bxi, int byi,
                                        int bzi, unsigned char *dsm, uint64_t *full,
                                        dc::BPView *sv, int4 *vtab, unsigned &it) {
-  constexpr size_t STAGE_BYTES = (size_t)TB_BH * TB_BWW * sizeof(T);
-  float2 *wtile0 = (float2 *)(dsm + TB_NS * STAGE_BYTES);
+  constexpr bool PAIRS = TileShape<T>::PAIRS;
+  constexpr int BWN = TileShape<T>::BWN, BWW = TileShape<T>::BWW;
+  constexpr size_t STAGE_BYTES = (size_t)TB_BH * BWW * sizeof(T);
+  float2 *wtile0 = (float2 *)(dsm + TB_NS * STAGE_BYTES);  // converted tiles (not PAIRS)
   const char *sb = reinterpret_cast<const char *>(dsm);
 
   const int tid = threadIdx.y * TB_TX + threadIdx.x;
@@ -349,7 +376,7 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
         good &= __shfl_xor_sync(0xffffffffu, good, o);
       }
       if (vi < nvc && cr == 0) {
-        int4 t = make_int4(0, 0, FP_GLOBAL, TB_BWW);
+        int4 t = make_int4(0, 0, FP_GLOBAL, BWW);
         if (good && fabsf(umin) < 1e6f && fabsf(umax) < 1e6f && fabsf(vmin) < 1e6f &&
             fabsf(vmax) < 1e6f) {
           constexpr int ALIGN = 16 / (int)sizeof(T);  // TMA x offset: 16-byte multiple
@@ -358,11 +385,11 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
           int x0 = j0 & ~(ALIGN - 1);
           int ncol = j1 - x0 + 1, nrow = r1 - r0 + 1;
           if (j1 < 0 || x0 >= a.W || r1 < 0 || r0 >= a.H) {
-            t = make_int4(x0, r0, FP_SKIP, TB_BWW);
-          } else if (nrow <= TB_BH && ncol <= TB_BWN) {
-            t = make_int4(x0, r0, FP_NARROW, TB_BWN);
-          } else if (nrow <= TB_BH && ncol <= TB_BWW) {
-            t = make_int4(x0, r0, FP_WIDE, TB_BWW);
+            t = make_int4(x0, r0, FP_SKIP, BWW);
+          } else if (nrow <= TB_BH && ncol <= BWN) {
+            t = make_int4(x0, r0, FP_NARROW, BWN);
+          } else if (nrow <= TB_BH && ncol <= BWW) {
+            t = make_int4(x0, r0, FP_WIDE, BWW);
           }
         }
         vtab[vi] = t;
@@ -374,10 +401,10 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
       unsigned char *dst = dsm + s * STAGE_BYTES;
       dc::fence_proxy_async();
       if (t.z == FP_NARROW) {
-        dc::mbar_arrive_expect_tx(&full[s], TB_BWN * TB_BH * sizeof(T));
+        dc::mbar_arrive_expect_tx(&full[s], BWN * TB_BH * sizeof(T));
         dc::tma_load_3d(dst, tmn, t.x, t.y, b * a.V + c0 + vi, &full[s]);
       } else if (t.z == FP_WIDE) {
-        dc::mbar_arrive_expect_tx(&full[s], TB_BWW * TB_BH * sizeof(T));
+        dc::mbar_arrive_expect_tx(&full[s], BWW * TB_BH * sizeof(T));
         dc::tma_load_3d(dst, tmw, t.x, t.y, b * a.V + c0 + vi, &full[s]);
       } else {
         dc::mbar_arrive(&full[s]);
@@ -394,15 +421,19 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
       if (a.scale) sc = a.scale[(size_t)b * a.V + i];
       bool w_ok = dc::mbar_wait_bounded(&full[s], (it / TB_NS) & 1, err);
       float2 *wt = wtile0 + (size_t)(it & 1) * TB_BH * TB_S2;
-      const unsigned wt_off = (unsigned)((const unsigned char *)wt - dsm);  // bytes
+      // the pair tile (bytes from dsm) and its row stride: the converted tile,
+      // or with PAIRS the TMA stage itself (row stride = box width)
+      const unsigned wt_off = PAIRS ? s * (unsigned)STAGE_BYTES
+                                    : (unsigned)((const unsigned char *)wt - dsm);
+      const unsigned rs = PAIRS ? (unsigned)t.w * 8u : (unsigned)(TB_S2 * 8);
       // tile byte offset minus the floor's exponent bits of a row and a column
-      const unsigned cbg = wt_off - kFloorBits * (unsigned)(TB_S2 * 8 + 8);
+      const unsigned cbg = wt_off - kFloorBits * (rs + 8u);
       const bool staged = (t.z == FP_NARROW || t.z == FP_WIDE);
-      if (w_ok && staged) {
+      if (!PAIRS && w_ok && staged) {
         // raw box -> FP32 pair tile (times the FP16 scale)
         const T *raw = (const T *)(dsm + s * STAGE_BYTES);
         const int bw = t.w;
-        if (sizeof(T) == 4) {
+        if constexpr (sizeof(T) == 4) {
           // four pairs per thread and step: one 16-byte load (+ the next
           // element) and two 16-byte stores
           const int lg = (bw == TB_BWN) ? 3 : 4;  // log2 of the groups per row
@@ -415,7 +446,7 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
             dst[0] = make_float4(v.x, v.y - v.x, v.y, v.z - v.y);
             dst[1] = make_float4(v.z, v.w - v.z, v.w, nx - v.w);
           }
-        } else {
+        } else if constexpr (sizeof(T) == 2) {
           // 16-bit storage: four values per 8-byte load, converted (and
           // scaled) to FP32 pairs with two 16-byte stores.  A BF16 value is
           // the upper half of the FP32 with the same bits, so its conversion
@@ -451,6 +482,16 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
           }
         }
       }
+      if constexpr (PAIRS) {
+        // the pair left of column 0 (fill zero from the copy) is (0, g[r][0]):
+        // its difference is the first column's value, which the tile holds
+        // whenever it reaches left of the detector (x0 < 0)
+        if (w_ok && staged && t.x < 0 && tid < TB_BH) {
+          float2 *row = reinterpret_cast<float2 *>(dsm + wt_off) + (size_t)tid * t.w;
+          row[-1 - t.x].y = row[-t.x].x;
+          dc::fence_proxy_async();  // before a later copy into this stage
+        }
+      }
       if (__syncthreads_or(!w_ok)) {
         ok = false;
         break;
@@ -472,7 +513,7 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
           float u = fminf(fmaxf(fmaf(U0, rw, cul), 0.0f), umx), fu;
           int j = dc::floor_frac(u, fu);
           // byte offset of column j, minus the floor's exponent bits per row
-          const unsigned cbc = wt_off + (unsigned)j * 8u - kFloorBits * (unsigned)(TB_S2 * 8);
+          const unsigned cbc = wt_off + (unsigned)j * 8u - kFloorBits * rs;
           float vb = fmaf(V0, rw, cvl), dv = dV * rw;
           // v is affine in k: the column stays inside the tile if both ends do
           float vlast = fmaf((float)(NZ - 1), dv, vb);
@@ -482,8 +523,8 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
               float kf = (float)k;
               const float v = fmaf(kf, dv, vb);
               const float tv = __fadd_rd(v, kM), fv = v - (tv - kM);
-              const unsigned off = __float_as_uint(tv) * (unsigned)(TB_S2 * 8) + cbc;
-              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + TB_S2 * 8);
+              const unsigned off = __float_as_uint(tv) * rs + cbc;
+              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + rs);
               float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
               float val = fmaf(fv, x1 - x0, x0);
               float ez = fmaf(kf, a.dz, ez0);
@@ -497,8 +538,8 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
               float kf = (float)k;
               const float v = fminf(fmaxf(fmaf(kf, dv, vb), 0.0f), vmx);
               const float tv = __fadd_rd(v, kM), fv = v - (tv - kM);
-              const unsigned off = __float_as_uint(tv) * (unsigned)(TB_S2 * 8) + cbc;
-              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + TB_S2 * 8);
+              const unsigned off = __float_as_uint(tv) * rs + cbc;
+              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + rs);
               float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
               float val = fmaf(fv, x1 - x0, x0);
               float ez = fmaf(kf, a.dz, ez0);
@@ -525,9 +566,8 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
               const float v = fmaf(fmaf(kf, dV, V0), rw, cvl);
               const float tu = __fadd_rd(u, kM), tv = __fadd_rd(v, kM);
               const float fu = u - (tu - kM), fv = v - (tv - kM);
-              const unsigned off = __float_as_uint(tv) * (unsigned)(TB_S2 * 8) +
-                                   __float_as_uint(tu) * 8u + cbg;
-              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + TB_S2 * 8);
+              const unsigned off = __float_as_uint(tv) * rs + __float_as_uint(tu) * 8u + cbg;
+              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + rs);
               float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
               float val = fmaf(fv, x1 - x0, x0);
               float ez = fmaf(kf, a.dz, ez0);
@@ -544,9 +584,8 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
               const float v = fminf(fmaxf(fmaf(fmaf(kf, dV, V0), rw, cvl), 0.0f), vmx);
               const float tu = __fadd_rd(u, kM), tv = __fadd_rd(v, kM);
               const float fu = u - (tu - kM), fv = v - (tv - kM);
-              const unsigned off = __float_as_uint(tv) * (unsigned)(TB_S2 * 8) +
-                                   __float_as_uint(tu) * 8u + cbg;
-              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + TB_S2 * 8);
+              const unsigned off = __float_as_uint(tv) * rs + __float_as_uint(tu) * 8u + cbg;
+              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + rs);
               float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
               float val = fmaf(fv, x1 - x0, x0);
               float ez = fmaf(kf, a.dz, ez0);
@@ -933,15 +972,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 3-D map over g^F viewed as [B*V][H][W] with a box of bw x TB_BH x 1
+// bytes per g^F pixel of a storage form
+int pixel_bytes(int dtype) { return dtype == DC_F32 ? 4 : dtype == DC_F32X2 ? 8 : 2; }
+
+// 3-D map over g^F viewed as [B*V][H][W] with a box of bw x TB_BH x 1 (a
+// DC_F32X2 pair is one 8-byte element: the copy moves its bits)
 bool make_map(CUtensorMap *m, const void *base, int dtype, int W, int H, long long nimg,
               int bw) {
   auto fn = encode_fn();
   if (!fn) return false;
-  int es = (dtype == DC_F32) ? 4 : 2;
-  CUtensorMapDataType t = (dtype == DC_F32)    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                          : (dtype == DC_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  int es = pixel_bytes(dtype);
+  CUtensorMapDataType t = (dtype == DC_F32)     ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                          : (dtype == DC_F32X2) ? CU_TENSOR_MAP_DATA_TYPE_UINT64
+                          : (dtype == DC_BF16)  ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nimg};
   cuuint64_t strides[2] = {(cuuint64_t)W * es, (cuuint64_t)W * H * es};
   cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)TB_BH, 1};
@@ -972,7 +1016,7 @@ int launch_bp_tma_nz(const dc_geometry *g, BPArgs &a, bool kahan, cudaStream_t s
 }
 
 bool tma_ok(const void *base, int W, int dtype) {
-  int es = (dtype == DC_F32) ? 4 : 2;
+  int es = pixel_bytes(dtype);
   return ((size_t)W * es) % 16 == 0 && ((uintptr_t)base & 15) == 0 && encode_fn() != nullptr;
 }
 
@@ -983,8 +1027,8 @@ int launch_bp_tma(const dc_geometry *g, BPArgs &a, int dtype, bool kahan, cudaSt
   if (!tma_ok(a.gF, a.W, dtype) || getenv("DC_BP_NO_TMA")) return DC_OK;
   CUtensorMap mn, mw;
   long long nimg = (long long)a.B * a.V;
-  if (!make_map(&mn, a.gF, dtype, a.W, a.H, nimg, TB_BWN) ||
-      !make_map(&mw, a.gF, dtype, a.W, a.H, nimg, TB_BWW))
+  if (!make_map(&mn, a.gF, dtype, a.W, a.H, nimg, TileShape<T>::BWN) ||
+      !make_map(&mw, a.gF, dtype, a.W, a.H, nimg, TileShape<T>::BWW))
     return DC_OK;
   int rc = (g->bp_nz == 16) ? launch_bp_tma_nz<T, 16>(g, a, kahan, st, mn, mw)
                             : launch_bp_tma_nz<T, 32>(g, a, kahan, st, mn, mw);
@@ -1038,7 +1082,7 @@ int backproject_check(const dc_geometry *g, int B, const void *gF, int dtype,
   if (!gF || !vol) return fail(DC_ERR_ARG, std::string(who) + ": NULL gF or vol");
   if (flags & ~(DC_ACCUM | DC_KAHAN | DC_RELU))
     return fail(DC_ERR_ARG, std::string(who) + ": unknown flag");
-  if (dtype != DC_F32 && dtype != DC_BF16 && dtype != DC_F16)
+  if (dtype != DC_F32 && dtype != DC_BF16 && dtype != DC_F16 && dtype != DC_F32X2)
     return fail(DC_ERR_ARG, std::string(who) + ": unknown dtype");
   if (dtype == DC_F16 && !gF_scale)
     return fail(DC_ERR_ARG, std::string(who) + ": DC_F16 needs gF_scale");
@@ -1056,6 +1100,7 @@ int backproject_slab(const dc_geometry *g, int B, const void *gF, int dtype,
   int rc;
   switch (dtype) {
     case DC_F32: rc = launch_bp_tma<float>(g, a, dtype, kahan, st, used); break;
+    case DC_F32X2: rc = launch_bp_tma<float2>(g, a, dtype, kahan, st, used); break;
     case DC_BF16: rc = launch_bp_tma<__nv_bfloat16>(g, a, dtype, kahan, st, used); break;
     default: rc = launch_bp_tma<__half>(g, a, dtype, kahan, st, used); break;
   }
@@ -1105,6 +1150,7 @@ int dc_backproject(const dc_geometry *g, int B, const void *gF, int dtype,
   bool used = false;
   switch (dtype) {
     case DC_F32: rc = launch_bp_tma<float>(g, a, dtype, kahan, st, &used); break;
+    case DC_F32X2: rc = launch_bp_tma<float2>(g, a, dtype, kahan, st, &used); break;
     case DC_BF16: rc = launch_bp_tma<__nv_bfloat16>(g, a, dtype, kahan, st, &used); break;
     case DC_F16: rc = launch_bp_tma<__half>(g, a, dtype, kahan, st, &used); break;
     default: return dc::fail(DC_ERR_ARG, "dc_backproject: unknown dtype");
@@ -1118,6 +1164,10 @@ int dc_backproject(const dc_geometry *g, int B, const void *gF, int dtype,
     case DC_F32:
       if (kahan) k_bp3d<float, true><<<grid, blk, 0, st>>>(a);
       else k_bp3d<float, false><<<grid, blk, 0, st>>>(a);
+      break;
+    case DC_F32X2:
+      if (kahan) k_bp3d<float2, true><<<grid, blk, 0, st>>>(a);
+      else k_bp3d<float2, false><<<grid, blk, 0, st>>>(a);
       break;
     case DC_BF16:
       if (kahan) k_bp3d<__nv_bfloat16, true><<<grid, blk, 0, st>>>(a);
@@ -1242,9 +1292,11 @@ int build_batch_tables(dc_batch *b) {
     P.a.dx = (float)d.voxel[0];
     P.a.dy = (float)d.voxel[1];
     P.a.dz = (float)d.voxel[2];
-    if (!make_map(&maps[2 * t], b->gF[i], b->dtype, d.det_cols, d.det_rows, d.n_views, TB_BWN) ||
+    const bool pairs = (b->dtype == DC_F32X2);
+    if (!make_map(&maps[2 * t], b->gF[i], b->dtype, d.det_cols, d.det_rows, d.n_views,
+                  pairs ? TB_PBWN : TB_BWN) ||
         !make_map(&maps[2 * t + 1], b->gF[i], b->dtype, d.det_cols, d.det_rows, d.n_views,
-                  TB_BWW))
+                  pairs ? TB_PBWW : TB_BWW))
       return dc::fail(DC_ERR_CUDA, "dc_batch: tensor map encoding failed");
     P.tmn = b->d_maps + 2 * t;
     P.tmw = b->d_maps + 2 * t + 1;
@@ -1289,7 +1341,7 @@ int dc_batch_create(int n, dc_geometry *const *geoms, int dtype, unsigned flags,
   *out = nullptr;
   if (n < 1 || n > DC_MAX_BATCH)
     return dc::fail(DC_ERR_ARG, "dc_batch_create: 1 <= n <= " + std::to_string(DC_MAX_BATCH));
-  if (dtype != DC_F32 && dtype != DC_BF16 && dtype != DC_F16)
+  if (dtype != DC_F32 && dtype != DC_BF16 && dtype != DC_F16 && dtype != DC_F32X2)
     return dc::fail(DC_ERR_ARG, "dc_batch_create: unknown dtype");
   if (flags & ~(DC_KAHAN | DC_RELU | DC_PERSISTENT_FILTER))
     return dc::fail(DC_ERR_ARG,
@@ -1297,7 +1349,7 @@ int dc_batch_create(int n, dc_geometry *const *geoms, int dtype, unsigned flags,
   if (!encode_fn()) return dc::fail(DC_ERR_UNSUPPORTED, "dc_batch_create: no TMA encoder");
   int dev = -1;
   cudaGetDevice(&dev);
-  int es = (dtype == DC_F32) ? 4 : 2;
+  int es = pixel_bytes(dtype);
   for (int i = 0; i < n; ++i) {
     if (!geoms[i]) return dc::fail(DC_ERR_ARG, "dc_batch_create: NULL geometry");
     if (geoms[i]->device != dev)
@@ -1386,6 +1438,7 @@ int dc_batch_run(dc_batch *b, const float *const *g, const float *const *W, floa
   int rc = DC_OK;
   switch (b->dtype) {
     case DC_F32: rc = launch_batched_t<float>(b, run, st); break;
+    case DC_F32X2: rc = launch_batched_t<float2>(b, run, st); break;
     case DC_BF16: rc = launch_batched_t<__nv_bfloat16>(b, run, st); break;
     default: rc = launch_batched_t<__half>(b, run, st); break;
   }

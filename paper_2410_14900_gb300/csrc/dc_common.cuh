@@ -51,6 +51,7 @@ enum KernelId {
   KID_SMOOTH,
   KID_ADJ_S,
   KID_FILTER_BATCHED,
+  KID_TO_PAIRS,
   KID_COUNT
 };
 

@@ -426,7 +426,7 @@ constexpr int BP2_TX = 32 * BP2_NQ;
 constexpr int BP2_TY = 8 * BP2_RY;
 constexpr int BP2_MC = 12;  // angles per stage (2 stages: 4 CTAs per SM at 512 s-bins)
 
-enum { OUT_F32 = 0, OUT_BF16 = 1, OUT_F32_ABSMAX = 2 };
+enum { OUT_F32 = 0, OUT_BF16 = 1, OUT_F32_ABSMAX = 2, OUT_F32_SLOT = 3 };
 
 struct BP2Args {
   const float *sino;  // [n][n_mu][NSp], pre-scaled by the Joseph and mu scales
@@ -440,6 +440,7 @@ struct BP2Args {
   int weight;          // WT_NONE / WT_COS / WT_D
   int out_kind;        // OUT_*
   void *out;           // user [B][V][H][W] (f32 or bf16) or scratch [n][H][Wp] f32
+                       // (OUT_F32_ABSMAX, OUT_F32_SLOT)
   int Wp;
   unsigned *absmax;    // [n] (OUT_F32_ABSMAX)
   unsigned *err;
@@ -482,7 +483,8 @@ __device__ __forceinline__ bool group_sync_or(int id, bool pred) {
 // its two mbarriers (initialised by the caller), `bmu` its per-angle
 // constants; `it` counts the angle chunks the group has staged so far (the
 // stage and the barrier phase of the next chunk follow from it).  Returns
-// false if a bounded wait gave up.
+// false if a bounded wait gave up.  OUT_F32_SLOT writes slot `slot` of the
+// scratch without the absmax.
 //
 // MULTI: ds < pitch, where the transposed Joseph hat of an angle (half-width
 // 1/winv s-bins, at most 3 for ds >= pitch/3) covers up to six taps; those
@@ -672,7 +674,7 @@ __device__ __forceinline__ bool bp2d_tile(const BP2Args &a, int n, int slot, int
         float l2 = fmaf(x, x, fmaf(y, y, fv.D * fv.D));
         val *= (a.weight == WT_D) ? l2 : fv.D * rsqrtf(l2);
       }
-      if (a.out_kind == OUT_F32_ABSMAX) {
+      if (a.out_kind == OUT_F32_ABSMAX || a.out_kind == OUT_F32_SLOT) {
         ((float *)a.out)[((size_t)slot * a.H + r) * a.Wp + j] = val;
         lmax = fmaxf(lmax, fabsf(val));
       } else {
@@ -729,6 +731,35 @@ __global__ void k_to_f16(const float *__restrict__ src, const unsigned *__restri
     int r = (int)(i / W), j = (int)(i % W);
     float val = src[((size_t)n * H + r) * Wp + j] * inv;
     dst[((size_t)b * V + v) * np + i] = __float2half_rn(val);
+  }
+}
+
+// FP32 pair storage (DC_F32X2): pixel (r, c) of g^F becomes the pair
+// (g[r][c], g[r][c+1] - g[r][c]), with g[r][W] = 0 (the detector's zero
+// extension), the tap pair of the backprojection's row interpolation.  A
+// thread converts two neighbouring pixels: three loads of the L2-resident
+// scratch row, one 16-byte store (W even) or two 8-byte stores.
+__global__ void k_to_pairs(const float *__restrict__ src, int H, int W, int Wp, int V, int B,
+                           int v0, int b0, float2 *__restrict__ dst) {
+  const int n = blockIdx.y;
+  const int v = v0 + n / B, b = b0 + n % B;
+  const int half = (W + 1) >> 1;  // pixel pairs per row
+  const size_t np = (size_t)H * W;
+  float2 *out = dst + ((size_t)b * V + v) * np;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)H * half;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / half), j = 2 * (int)(i - (size_t)r * half);
+    const float *row = src + ((size_t)n * H + r) * Wp;
+    const float g0 = row[j];
+    const float g1 = (j + 1 < W) ? row[j + 1] : 0.0f;
+    const float g2 = (j + 2 < W) ? row[j + 2] : 0.0f;
+    float2 *o = out + (size_t)r * W + j;
+    if ((W & 1) == 0) {
+      *reinterpret_cast<float4 *>(o) = make_float4(g0, g1 - g0, g1, g2 - g1);
+    } else {
+      o[0] = make_float2(g0, g1 - g0);
+      if (j + 1 < W) o[1] = make_float2(g1, g2 - g1);
+    }
   }
 }
 
@@ -1171,10 +1202,12 @@ int filter_check(const dc_geometry *g, int B, const float *gin, const void *gF, 
   int rc = check_common(g, B, who);
   if (rc) return rc;
   if (!gin || !gF) return fail(DC_ERR_ARG, std::string(who) + ": NULL g or gF");
-  if (dtype != DC_F32 && dtype != DC_BF16 && dtype != DC_F16)
+  if (dtype != DC_F32 && dtype != DC_BF16 && dtype != DC_F16 && dtype != DC_F32X2)
     return fail(DC_ERR_ARG, std::string(who) + ": unknown dtype");
   if (dtype == DC_F16 && !gF_scale)
     return fail(DC_ERR_ARG, std::string(who) + ": DC_F16 needs gF_scale");
+  if (dtype == DC_F32X2 && ((uintptr_t)gF & 15) != 0)
+    return fail(DC_ERR_ARG, std::string(who) + ": DC_F32X2 g^F must be 16-byte aligned");
   const dc_geometry_desc &d = g->d;
   if (3.0 * d.ds < d.pitch * (1.0 - 1e-12))
     return fail(DC_ERR_UNSUPPORTED, std::string(who) + ": ds < pitch/3 is not supported");
@@ -1211,6 +1244,17 @@ int filter_chunk(const dc_geometry *g, const float *gin, const float *W, void *g
     k_to_f16<<<grid, 256, 0, st>>>(g->w_img, g->w_absmax, d.det_rows, d.det_cols, g->Wp,
                                    d.n_views, bc, v0, b0, (__half *)gF, gF_scale);
     DC_CHECK_LAUNCH("k_to_f16");
+  } else if (dtype == DC_F32X2) {
+    // g^F of the chunk into the work area (L2-resident), then the pairs
+    ba.out_kind = OUT_F32_SLOT;
+    ba.out = g->w_img;
+    if ((rc = launch_bp2d(g, ba, st))) return rc;
+    const int pairs_per_img = d.det_rows * ((d.det_cols + 1) / 2);
+    dim3 grid((unsigned)std::min(64, (pairs_per_img + 255) / 256), n_img);
+    ProfScope ps(KID_TO_PAIRS, st);
+    k_to_pairs<<<grid, 256, 0, st>>>(g->w_img, d.det_rows, d.det_cols, g->Wp, d.n_views, bc, v0,
+                                     b0, (float2 *)gF);
+    DC_CHECK_LAUNCH("k_to_pairs");
   } else {
     ba.out_kind = (dtype == DC_BF16) ? OUT_BF16 : OUT_F32;
     ba.out = gF;
@@ -1249,6 +1293,8 @@ int batch_filter_create(int n, dc_geometry *const *geoms, int dtype, void *const
                         float *const *scale, BatchFilterPlan **out) {
   *out = nullptr;
   if (n < 1 || n > DC_BF_MAX) return fail(DC_ERR_ARG, "batched filter: 1 <= n <= 32");
+  if (dtype == DC_F32X2)  // the pairs come from a pass over the finished image
+    return fail(DC_ERR_UNSUPPORTED, "batched filter: DC_F32X2 uses the chunked filter");
   int dev = 0;
   DC_CUDA(cudaGetDevice(&dev));
   cudaFuncAttributes fa;

@@ -74,9 +74,7 @@ def autotune(geom: api.Geometry, dtype: str = "f32", use_cache: bool = True,
     cap = api.dc_geometry_get_tuning(geom)["chunk_capacity"]
     dev = torch.device("cuda", torch.cuda.current_device())
     g = torch.rand((1, geom.V, geom.H, geom.W), device=dev)
-    gF = torch.empty((1, geom.V, geom.H, geom.W), device=dev,
-                     dtype={"f32": torch.float32, "bf16": torch.bfloat16,
-                            "f16": torch.float16}[dtype])
+    gF = torch.empty(api.gF_shape(geom, 1, dtype), device=dev, dtype=api._DTYPES[dtype][1])
     sc = torch.empty((1, geom.V), device=dev) if dtype == "f16" else None
     vol = torch.empty((1,) + geom.vol_shape, device=dev)
     res = {"filter_ms": {}, "bp_ms": {}}

@@ -26,10 +26,13 @@ def _problems():
     return out
 
 
-# FP32: the method's 1e-4 target; BF16 / FP16 storage of g^F: the stated
-# storage error of those forms (measured ~7e-4 and ~1e-4 on these problems)
+# FP32 and FP32 pairs: the method's 1e-4 target; BF16 / FP16 storage of g^F:
+# the stated storage error of those forms (measured ~7e-4 and ~1e-4 on these
+# problems).  A pair batch keeps the chunked filters even when the
+# persistent one is asked for.
 @pytest.mark.parametrize("persistent", [False, True])
-@pytest.mark.parametrize("dtype,tol", [("f32", 1e-4), ("bf16", 3e-3), ("f16", 5e-4)])
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-4), ("f32x2", 1e-4), ("bf16", 3e-3),
+                                       ("f16", 5e-4)])
 def test_batched_matches_oracle(dtype, tol, persistent):
     probs = _problems()
     geoms = [p[1] for p in probs]
@@ -40,7 +43,8 @@ def test_batched_matches_oracle(dtype, tol, persistent):
     W_list = [torch.as_tensor(Wn, device="cuda") for Wn in W_np]
     # one problem keeps the default weight 1/2
     W_list[1] = None
-    batch = api.Batch(geoms, dtype=dtype, kahan=(dtype != "f32"), persistent_filter=persistent)
+    batch = api.Batch(geoms, dtype=dtype, kahan=(dtype in ("bf16", "f16")),
+                      persistent_filter=persistent)
     vols = [torch.full(geom.vol_shape, float("nan"), device="cuda") for geom in geoms]
     batch.run(g_list, vols, W_list)
     torch.cuda.synchronize()

@@ -29,7 +29,7 @@ def _projections(w, device="cuda"):
 
 
 @pytest.mark.parametrize("name", ["circle_arc512", "paper400"])
-@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("storage", ["f32", "f32x2", "bf16"])
 def test_backprojection_full_size_sampled_voxels(name, storage):
     w = synth.workload(name)
     gg, og = _geoms(w)
@@ -39,7 +39,11 @@ def test_backprojection_full_size_sampled_voxels(name, storage):
     gF = torch.randn((1, V, H, W), device="cuda", generator=gen)
     if storage == "bf16":
         gF = gF.to(torch.bfloat16)
-    vol = api.dc_backproject(gg, gF, kahan=(storage != "f32"))
+    stored = gF
+    if storage == "f32x2":   # (value, right difference) pairs of the same values
+        right = torch.cat([gF[..., 1:], torch.zeros_like(gF[..., :1])], dim=-1)
+        stored = torch.stack([gF, right - gF], dim=-1).contiguous()
+    vol = api.dc_backproject(gg, stored, kahan=(storage == "bf16"))
     nvox = w.vol_shape[0] * w.vol_shape[1] * w.vol_shape[2]
     flat = np.random.default_rng(3).choice(nvox, size=4096, replace=False)
     # the oracle sees exactly the stored values.  White-noise data turn any
@@ -64,6 +68,21 @@ def test_filter_full_size_sampled_views(name, views):
     for t, i in enumerate(views):
         err = rel_l2(gF[0, i].double().cpu().numpy(), ref[t])
         assert err < 1e-4, (i, err)
+
+
+def test_pair_filter_full_size_equals_fp32_filter():
+    """The benchmark's storage form at its size: the filter's pairs are the
+    FP32 filter's values (checked against the oracle above) and their
+    right differences, bit for bit."""
+    w = synth.workload("circle_arc512")
+    gg, _ = _geoms(w)
+    g = _projections(w)
+    gF, _ = api.dc_filter(gg, g, None, "f32")
+    gP, _ = api.dc_filter(gg, g, None, "f32x2")
+    torch.cuda.synchronize()
+    assert torch.equal(gP[..., 0], gF)
+    right = torch.cat([gF[..., 1:], torch.zeros_like(gF[..., :1])], dim=-1)
+    assert torch.equal(gP[..., 1], right - gF)
 
 
 def test_sinusoid_full_chain_sampled_voxels():

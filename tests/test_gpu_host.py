@@ -36,7 +36,7 @@ def test_host_pipeline_storage_forms_and_pageable_memory():
     geom = api.Geometry(case.desc, case.P, case.vdl)
     g = phantom_projections(case).astype(np.float32)
     gd = torch.as_tensor(g, device="cuda")
-    for dt in ("bf16", "f16"):
+    for dt in ("bf16", "f16", "f32x2"):
         vol_host = torch.empty((1,) + geom.vol_shape)          # pageable on purpose
         api.dc_reconstruct_host(geom, torch.from_numpy(g), vol_host, dtype=dt, kahan=True)
         torch.cuda.synchronize()
