@@ -234,7 +234,7 @@ def interp_peaks(L, dev) -> dict:
     stream = torch.cuda.current_stream()
     out = {}
     for kind, name in enumerate(("joseph_step", "hat_pair", "bilinear_sample",
-                                 "weighted_sample")):
+                                 "weighted_sample", "quad_weighted_sample")):
         for _ in range(2):
             L.dc_microbench(kind, nb, 100, sink.data_ptr(), stream.cuda_stream)
         torch.cuda.synchronize()

@@ -427,8 +427,11 @@ const char *dc_version(void);
  * so that its practical peak can be timed (CUDA events around the call):
  * kind 0 the Joseph step of the line sums, 1 the transposed-hat pair of the
  * 2-D backprojection, 2 the bilinear sample of the cone-beam
- * backprojection, 3 that sample times the voxel weight 1/|X - a|^2.  n_blocks CTAs of 512 threads each run iters x 32 steps
- * per thread; sink (device, n_blocks*512 floats) receives their sums.
+ * backprojection, 3 that sample times the voxel weight 1/|X - a|^2, 4 the
+ * weighted sample from a tile of quads (both rows' value and difference of
+ * a pixel), two voxels per step in packed FP32x2.  n_blocks CTAs of 512
+ * threads each run iters x 32 samples per thread; sink (device,
+ * n_blocks*512 floats) receives their sums.
  */
 int dc_microbench(int kind, int n_blocks, int iters, float *sink, void *stream);
 

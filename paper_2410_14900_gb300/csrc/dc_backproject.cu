@@ -297,6 +297,23 @@ __device__ __forceinline__ float2 ldpair(const char *sb, unsigned off) {
   return *reinterpret_cast<const float2 *>(sb + off);
 }
 
+// bilinear sample from the pair tile: the rows at byte offsets off and
+// off + RS, each interpolated across columns by its (value, difference)
+// pair, then across the two rows
+template <unsigned RS>
+__device__ __forceinline__ float tile_sample(const char *sb, unsigned off, float fu, float fv) {
+  const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + RS);
+  const float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
+  return fmaf(fv, x1 - x0, x0);
+}
+
+// packed (two-lane) floor and fraction with the rounded-down offset: t holds
+// floor(x) + kM (its bits are kFloorBits + floor(x)), f = x - floor(x) exactly
+__device__ __forceinline__ void floor_frac2(float2 x, float2 &t, float2 &f) {
+  t = __fadd2_rd(x, make_float2(kM, kM));
+  f = __ffma2_rn(__fadd2_rn(t, make_float2(-kM, -kM)), make_float2(-1.0f, -1.0f), x);
+}
+
 // One CTA backprojects one box of 16 x 16 x NZ voxels (box indices bxi, byi
 // and bzi = batch item * z-blocks + z-block) over every view.  `it` is the
 // CTA's running view counter (mbarrier stage and parity), carried across
@@ -338,14 +355,29 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
   const size_t np = (size_t)a.H * a.W;
   const T *gbase = (const T *)a.gF + (size_t)b * a.V * np;
 
-  // With KAHAN each view chunk's terms are summed in plain FP32 into prt[],
-  // and the chunk sums are added to acc[] with Kahan compensation (cmp[]),
-  // so the compensated sum runs over the V / TB_VCH chunk sums rather than
+  // The column's voxels in pairs: element h of acc2 holds voxels h and
+  // h + NH, so that two voxels' positions, floors, weights and sums take one
+  // packed FP32x2 operation each (sm_100+; each half rounded as the scalar
+  // operation would round it).
+  // With KAHAN each view chunk's terms are summed in plain FP32 into prt2,
+  // and the chunk sums are added to acc2 with Kahan compensation (cmp2), so
+  // the compensated sum runs over the V / TB_VCH chunk sums rather than
   // every view: the FP32 error is that of a TB_VCH-term sum, at 1/TB_VCH of
-  // the per-view compensation cost.  Without KAHAN terms go to acc[].
-  float acc[NZ], cmp[NZ], prt[NZ];
+  // the per-view compensation cost.  Without KAHAN terms go to acc2.
+  constexpr int NH = NZ / 2;
+  float2 acc2[NH], cmp2[NH], prt2[NH];
 #pragma unroll
-  for (int k = 0; k < NZ; ++k) acc[k] = cmp[k] = prt[k] = 0.0f;
+  for (int h = 0; h < NH; ++h) acc2[h] = cmp2[h] = prt2[h] = make_float2(0.0f, 0.0f);
+  // a pair of terms val * wt into voxels (h, h + NH); one term into voxel k
+  auto add2 = [&](int h, float2 val, float2 wt) {
+    if (KAHAN) prt2[h] = __ffma2_rn(val, wt, prt2[h]);
+    else acc2[h] = __ffma2_rn(val, wt, acc2[h]);
+  };
+  auto add1 = [&](int k, float term) {
+    float2 &c = KAHAN ? prt2[k < NH ? k : k - NH] : acc2[k < NH ? k : k - NH];
+    if (k < NH) c.x += term;
+    else c.y += term;
+  };
 
   bool ok = true;
   for (int c0 = 0; c0 < a.V && ok; c0 += TB_VCH) {
@@ -425,9 +457,6 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
       // or with PAIRS the TMA stage itself (row stride = box width)
       const unsigned wt_off = PAIRS ? s * (unsigned)STAGE_BYTES
                                     : (unsigned)((const unsigned char *)wt - dsm);
-      const unsigned rs = PAIRS ? (unsigned)t.w * 8u : (unsigned)(TB_S2 * 8);
-      // tile byte offset minus the floor's exponent bits of a row and a column
-      const unsigned cbg = wt_off - kFloorBits * (rs + 8u);
       const bool staged = (t.z == FP_NARROW || t.z == FP_WIDE);
       if (!PAIRS && w_ok && staged) {
         // raw box -> FP32 pair tile (times the FP16 scale)
@@ -504,49 +533,41 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
       float dU = w.r0.z * a.dz, dV = w.r1.z * a.dz, dW = w.r2.z * a.dz;
       float ex = w.ca.x + xo, ey = w.ca.y + yo, ez0 = w.ca.z + zo;
       float rho2 = fmaf(ex, ex, ey * ey);
-      if (staged) {
+      // a staged view, with the tile's row stride RS (bytes) a constant: the
+      // second row's taps are an immediate offset from the first's
+      auto staged_view = [&](auto rs_const) {
+        constexpr unsigned RS = decltype(rs_const)::value;
+        // tile byte offset minus the floor's exponent bits of a row and a column
+        const unsigned cbg = wt_off - kFloorBits * (RS + 8u);
         const float cul = w.pp.x - (float)t.x, cvl = w.pp.y - (float)t.y;
         const float umx = (float)t.w - 1.001f, vmx = (float)TB_BH - 1.001f;
+        const float2 dz2 = make_float2(a.dz, a.dz), ez02 = make_float2(ez0, ez0);
+        const float2 rho22 = make_float2(rho2, rho2);
         if (w.ca.w != 0.0f) {
           // circle view: u and the depth do not change along the column
           float rw = dc::rcp_approx(W0);
           float u = fminf(fmaxf(fmaf(U0, rw, cul), 0.0f), umx), fu;
           int j = dc::floor_frac(u, fu);
           // byte offset of column j, minus the floor's exponent bits per row
-          const unsigned cbc = wt_off + (unsigned)j * 8u - kFloorBits * rs;
+          const unsigned cbc = wt_off + (unsigned)j * 8u - kFloorBits * RS;
           float vb = fmaf(V0, rw, cvl), dv = dV * rw;
+          const float2 vb2 = make_float2(vb, vb), dv2 = make_float2(dv, dv);
           // v is affine in k: the column stays inside the tile if both ends do
           float vlast = fmaf((float)(NZ - 1), dv, vb);
-          if (fminf(vb, vlast) >= 0.01f && fmaxf(vb, vlast) <= vmx - 0.01f) {
+          const bool inside = fminf(vb, vlast) >= 0.01f && fmaxf(vb, vlast) <= vmx - 0.01f;
 #pragma unroll
-            for (int k = 0; k < NZ; ++k) {
-              float kf = (float)k;
-              const float v = fmaf(kf, dv, vb);
-              const float tv = __fadd_rd(v, kM), fv = v - (tv - kM);
-              const unsigned off = __float_as_uint(tv) * rs + cbc;
-              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + rs);
-              float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
-              float val = fmaf(fv, x1 - x0, x0);
-              float ez = fmaf(kf, a.dz, ez0);
-              float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
-              if (KAHAN) prt[k] += term;
-              else acc[k] += term;
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < NZ; ++k) {
-              float kf = (float)k;
-              const float v = fminf(fmaxf(fmaf(kf, dv, vb), 0.0f), vmx);
-              const float tv = __fadd_rd(v, kM), fv = v - (tv - kM);
-              const unsigned off = __float_as_uint(tv) * rs + cbc;
-              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + rs);
-              float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
-              float val = fmaf(fv, x1 - x0, x0);
-              float ez = fmaf(kf, a.dz, ez0);
-              float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
-              if (KAHAN) prt[k] += term;
-              else acc[k] += term;
-            }
+          for (int h = 0; h < NH; ++h) {
+            const float2 kf = make_float2((float)h, (float)(h + NH));
+            float2 v = __ffma2_rn(kf, dv2, vb2);
+            if (!inside) v = make_float2(fminf(fmaxf(v.x, 0.0f), vmx), fminf(fmaxf(v.y, 0.0f), vmx));
+            float2 tv, fv;
+            floor_frac2(v, tv, fv);
+            const float2 val =
+                make_float2(tile_sample<RS>(sb, __float_as_uint(tv.x) * RS + cbc, fu, fv.x),
+                            tile_sample<RS>(sb, __float_as_uint(tv.y) * RS + cbc, fu, fv.y));
+            const float2 ez = __ffma2_rn(kf, dz2, ez02);
+            const float2 r2 = __ffma2_rn(ez, ez, rho22);
+            add2(h, val, make_float2(dc::rcp_approx(r2.x), dc::rcp_approx(r2.y)));
           }
         } else {
           // (u, v) = (affine in k) / (affine depth > 0): monotonic in k, so
@@ -556,44 +577,42 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
           float u0 = fmaf(U0, rw0, cul), ul = fmaf(fmaf(kl, dU, U0), rwl, cul);
           float v0 = fmaf(V0, rw0, cvl), vl = fmaf(fmaf(kl, dV, V0), rwl, cvl);
           const float m = 0.01f;  // margin for the rounding of the end points
-          if (fminf(u0, ul) >= m && fmaxf(u0, ul) <= umx - m && fminf(v0, vl) >= m &&
-              fmaxf(v0, vl) <= vmx - m) {
+          const bool inside = fminf(u0, ul) >= m && fmaxf(u0, ul) <= umx - m &&
+                              fminf(v0, vl) >= m && fmaxf(v0, vl) <= vmx - m;
+          const float2 dW2 = make_float2(dW, dW), W02 = make_float2(W0, W0);
+          const float2 dU2 = make_float2(dU, dU), U02 = make_float2(U0, U0);
+          const float2 dV2 = make_float2(dV, dV), V02 = make_float2(V0, V0);
+          const float2 cul2 = make_float2(cul, cul), cvl2 = make_float2(cvl, cvl);
 #pragma unroll
-            for (int k = 0; k < NZ; ++k) {
-              float kf = (float)k;
-              float rw = dc::rcp_approx(fmaf(kf, dW, W0));
-              const float u = fmaf(fmaf(kf, dU, U0), rw, cul);
-              const float v = fmaf(fmaf(kf, dV, V0), rw, cvl);
-              const float tu = __fadd_rd(u, kM), tv = __fadd_rd(v, kM);
-              const float fu = u - (tu - kM), fv = v - (tv - kM);
-              const unsigned off = __float_as_uint(tv) * rs + __float_as_uint(tu) * 8u + cbg;
-              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + rs);
-              float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
-              float val = fmaf(fv, x1 - x0, x0);
-              float ez = fmaf(kf, a.dz, ez0);
-              float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
-              if (KAHAN) prt[k] += term;
-              else acc[k] += term;
+          for (int h = 0; h < NH; ++h) {
+            const float2 kf = make_float2((float)h, (float)(h + NH));
+            const float2 dep = __ffma2_rn(kf, dW2, W02);
+            const float2 rw = make_float2(dc::rcp_approx(dep.x), dc::rcp_approx(dep.y));
+            float2 u = __ffma2_rn(__ffma2_rn(kf, dU2, U02), rw, cul2);
+            float2 v = __ffma2_rn(__ffma2_rn(kf, dV2, V02), rw, cvl2);
+            if (!inside) {
+              u = make_float2(fminf(fmaxf(u.x, 0.0f), umx), fminf(fmaxf(u.y, 0.0f), umx));
+              v = make_float2(fminf(fmaxf(v.x, 0.0f), vmx), fminf(fmaxf(v.y, 0.0f), vmx));
             }
-          } else {
-#pragma unroll
-            for (int k = 0; k < NZ; ++k) {
-              float kf = (float)k;
-              float rw = dc::rcp_approx(fmaf(kf, dW, W0));
-              const float u = fminf(fmaxf(fmaf(fmaf(kf, dU, U0), rw, cul), 0.0f), umx);
-              const float v = fminf(fmaxf(fmaf(fmaf(kf, dV, V0), rw, cvl), 0.0f), vmx);
-              const float tu = __fadd_rd(u, kM), tv = __fadd_rd(v, kM);
-              const float fu = u - (tu - kM), fv = v - (tv - kM);
-              const unsigned off = __float_as_uint(tv) * rs + __float_as_uint(tu) * 8u + cbg;
-              const float2 q0 = ldpair(sb, off), q1 = ldpair(sb, off + rs);
-              float x0 = fmaf(fu, q0.y, q0.x), x1 = fmaf(fu, q1.y, q1.x);
-              float val = fmaf(fv, x1 - x0, x0);
-              float ez = fmaf(kf, a.dz, ez0);
-              float term = val * dc::rcp_approx(fmaf(ez, ez, rho2));
-              if (KAHAN) prt[k] += term;
-              else acc[k] += term;
-            }
+            float2 tu, fu, tv, fv;
+            floor_frac2(u, tu, fu);
+            floor_frac2(v, tv, fv);
+            const unsigned oa = __float_as_uint(tv.x) * RS + __float_as_uint(tu.x) * 8u + cbg;
+            const unsigned ob = __float_as_uint(tv.y) * RS + __float_as_uint(tu.y) * 8u + cbg;
+            const float2 val = make_float2(tile_sample<RS>(sb, oa, fu.x, fv.x),
+                                           tile_sample<RS>(sb, ob, fu.y, fv.y));
+            const float2 ez = __ffma2_rn(kf, dz2, ez02);
+            const float2 r2 = __ffma2_rn(ez, ez, rho22);
+            add2(h, val, make_float2(dc::rcp_approx(r2.x), dc::rcp_approx(r2.y)));
           }
+        }
+      };
+      if (staged) {
+        if constexpr (PAIRS) {
+          if (t.w == BWN) staged_view(std::integral_constant<unsigned, BWN * 8u>());
+          else staged_view(std::integral_constant<unsigned, BWW * 8u>());
+        } else {
+          staged_view(std::integral_constant<unsigned, TB_S2 * 8u>());
         }
       } else if (t.z == FP_GLOBAL) {
         const T *img = gbase + (size_t)i * np;
@@ -607,20 +626,22 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
           float v = fmaf(fmaf(kf, dV, V0), rw, w.pp.y);
           float val = bilinear<T>(img, a.H, a.W, u, v) * sc;
           float ez = fmaf(kf, a.dz, ez0);
-          float term = val * __frcp_rn(fmaf(ez, ez, rho2));
-          if (KAHAN) prt[k] += term;
-          else acc[k] += term;
+          add1(k, val * __frcp_rn(fmaf(ez, ez, rho2)));
         }
       }
     }
     if (KAHAN && ok) {
+      auto kahan_step = [](float &acc, float &cmp, float &prt) {
+        const float y = prt - cmp;
+        const float tt = acc + y;
+        cmp = (tt - acc) - y;
+        acc = tt;
+        prt = 0.0f;
+      };
 #pragma unroll
-      for (int k = 0; k < NZ; ++k) {
-        const float y = prt[k] - cmp[k];
-        const float tt = acc[k] + y;
-        cmp[k] = (tt - acc[k]) - y;
-        acc[k] = tt;
-        prt[k] = 0.0f;
+      for (int h = 0; h < NH; ++h) {
+        kahan_step(acc2[h].x, cmp2[h].x, prt2[h].x);
+        kahan_step(acc2[h].y, cmp2[h].y, prt2[h].y);
       }
     }
   }
@@ -632,7 +653,7 @@ __device__ __forceinline__ bool bp_box(const BPArgs &a, float *vol, const CUtens
     int iz = z0 + k;
     if (iz >= a.z_end) break;
     size_t o = (size_t)b * nvox + ((size_t)iz * a.ny + iy) * a.nx + ix;
-    float f = acc[k];
+    float f = (k < NH) ? acc2[k].x : acc2[k - NH].y;
     if (a.flags & DC_ACCUM) f += vol[o];
     if ((a.flags & DC_RELU) && f < 0.0f) f = 0.0f;
     vol[o] = f;

@@ -13,6 +13,9 @@
 //           three interpolations, accumulate
 //   kind 3  kind 2 times the voxel weight 1/|X - a|^2 (the circle-view update
 //           of k_bp3d_tma: two more FMAs and a reciprocal)
+//   kind 4  kind 3 from a tile of quads (both rows' value and difference of
+//           a pixel in 16 bytes): one 16-byte load per sample, two samples
+//           (voxels k and k + 16 of a column) per step in packed FP32x2
 //
 // Every thread runs `iters` rounds of 32 unrolled steps; the result goes to
 // `sink` so that nothing is optimised away.  The measured steps per second
@@ -30,6 +33,9 @@ constexpr int MB_TILE = 16384;  // floats of the resident tile (64 KB)
 
 __device__ __forceinline__ float ldf(const char *sb, unsigned off) {
   return *reinterpret_cast<const float *>(sb + off);
+}
+__device__ __forceinline__ float4 ldq(const char *sb, unsigned off) {
+  return *reinterpret_cast<const float4 *>(sb + off);
 }
 
 __global__ void __launch_bounds__(MB_THREADS) k_microbench(int kind, int iters, float *sink) {
@@ -84,6 +90,34 @@ __global__ void __launch_bounds__(MB_THREADS) k_microbench(int kind, int iters, 
       }
     }
     acc = a2.x + a2.y;
+  } else if (kind == 4) {
+    // quad tile of 32 rows x 44 quads (row stride 704 bytes, 64 mod 128)
+    const float fu = 0.3f + 0.01f * (float)lane;
+    const float2 fu2 = make_float2(fu, fu);
+    const float dv = 0.93f, dz = 0.375f;
+    const float ez0 = -40.0f + 0.1f * (float)lane, rho2 = 5.0e5f + (float)warp;
+    const float2 M2 = make_float2(M, M), mM2 = make_float2(-M, -M), m12 = make_float2(-1.f, -1.f);
+    float2 a2 = make_float2(0.0f, 0.0f);
+    for (int it = 0; it < iters; ++it) {
+      const float vb = 1.0f + 0.25f * (float)(lane & 3) + 0.001f * (float)(it & 7);
+      const unsigned cbc = (unsigned)((2 * warp + (lane >> 2) + 2) * 16) - 0x4B400000u * 704u;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float2 kf = make_float2((float)k, (float)(k + 16));
+        const float2 v = __ffma2_rn(kf, make_float2(dv, dv), make_float2(vb, vb));
+        const float2 t = __fadd2_rd(v, M2);
+        const float2 f = __ffma2_rn(__fadd2_rn(t, mM2), m12, v);
+        const float4 qa = ldq(sb, __float_as_uint(t.x) * 704u + cbc);
+        const float4 qb = ldq(sb, __float_as_uint(t.y) * 704u + cbc);
+        const float2 xa = __ffma2_rn(fu2, make_float2(qa.z, qa.w), make_float2(qa.x, qa.y));
+        const float2 xb = __ffma2_rn(fu2, make_float2(qb.z, qb.w), make_float2(qb.x, qb.y));
+        const float2 val = make_float2(fmaf(f.x, xa.y - xa.x, xa.x), fmaf(f.y, xb.y - xb.x, xb.x));
+        const float2 ez = __ffma2_rn(kf, make_float2(dz, dz), make_float2(ez0, ez0));
+        const float2 r2 = __ffma2_rn(ez, ez, make_float2(rho2, rho2));
+        a2 = __ffma2_rn(val, make_float2(dc::rcp_approx(r2.x), dc::rcp_approx(r2.y)), a2);
+      }
+    }
+    acc = a2.x + a2.y;
   } else {
     // pair tile of 40 rows x 72 float2 (row stride 576 bytes)
     const float fu = 0.3f + 0.01f * (float)lane;
@@ -117,8 +151,8 @@ __global__ void __launch_bounds__(MB_THREADS) k_microbench(int kind, int iters, 
 }  // namespace
 
 extern "C" int dc_microbench(int kind, int n_blocks, int iters, float *sink, void *stream) {
-  if (kind < 0 || kind > 3 || n_blocks < 1 || iters < 1 || !sink)
-    return dc::fail(DC_ERR_ARG, "dc_microbench: kind 0..3, n_blocks >= 1, iters >= 1, sink");
+  if (kind < 0 || kind > 4 || n_blocks < 1 || iters < 1 || !sink)
+    return dc::fail(DC_ERR_ARG, "dc_microbench: kind 0..4, n_blocks >= 1, iters >= 1, sink");
   const size_t sm = sizeof(float) * MB_TILE;
   DC_CUDA(cudaFuncSetAttribute(k_microbench, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   k_microbench<<<n_blocks, MB_THREADS, sm, (cudaStream_t)stream>>>(kind, iters, sink);
