@@ -523,10 +523,10 @@ def batched_measure(args, dev, L):
     out = {"problems": len(ws), "views": [w.n_views for w in ws],
            "detectors": [[w.det_rows, w.det_cols] for w in ws],
            "volumes": [w.vol_shape[0] for w in ws], "voxel_view_updates": updates}
-    for dtype, persistent in (("f32", False), ("bf16", False), ("f32", True)):
-        batch = api.Batch(geoms, dtype=dtype, kahan=(dtype != "f32"),
-                          persistent_filter=persistent)
-        tuned = tune.autotune_batch(batch, g_list, vols, dtype=dtype, kahan=(dtype != "f32"))
+    for dtype, persistent in (("f32", False), ("bf16", False), ("f32", True), ("f32x2", False)):
+        kh = dtype in ("bf16", "f16")
+        batch = api.Batch(geoms, dtype=dtype, kahan=kh, persistent_filter=persistent)
+        tuned = tune.autotune_batch(batch, g_list, vols, dtype=dtype, kahan=kh)
         batch.capture(g_list, vols)
         ms = timed(batch.replay, args.steps)
         tag = dtype + ("_persistent_filter" if persistent else "")
@@ -534,13 +534,15 @@ def batched_measure(args, dev, L):
         out[f"{tag}_bp_nz"] = tuned["bp_nz"]
         batch.close()
         del batch
-    # one by one, each problem with its own tuned box depth (set above)
+    # one by one, each problem with its own tuned box depth (set above by the
+    # pair-storage tuning), in FP32 pair storage as the last batch
     def seq():
         for gm, g, v in zip(geoms, g_list, vols):
-            gF, _ = api.dc_filter(gm, g[None])
+            gF, _ = api.dc_filter(gm, g[None], None, "f32x2")
             api.dc_backproject(gm, gF, out=v[None])
-    out["f32_sequential_ms_per_batch"] = timed(seq, args.steps)
+    out["f32x2_sequential_ms_per_batch"] = timed(seq, args.steps)
     out["f32_graph_ms_per_volume"] = out["f32_graph_ms_per_batch"] / len(ws)
+    out["f32x2_graph_ms_per_volume"] = out["f32x2_graph_ms_per_batch"] / len(ws)
     for gm in geoms:
         api.dc_sync_status(gm)
         gm.close()
@@ -556,14 +558,15 @@ def paper_shape_measure(args, dev, L):
 
     w = synth.workload("paper400")
     geom = api.Geometry(w.desc_dict(), w.matrices(), w.orbit.vdl)
-    tuned = tune.autotune(geom, "f32", chunks=(8, 12, 16, 20, 25), nzs=(16, 32))
+    st = args.storage if args.storage in ("f32", "f32x2") else "f32"
+    tuned = tune.autotune(geom, st, chunks=(8, 12, 16, 20, 25), nzs=(16, 32))
     g = synth.project_phantom(w.phantoms()[0], w.orbit, w.det_rows, w.det_cols, w.pitch,
                               device=dev, dtype=torch.float32)[None].contiguous()
-    gF = torch.empty_like(g)
+    gF = torch.empty(api.gF_shape(geom, 1, st), device=dev)
     vol = torch.empty((1,) + geom.vol_shape, device=dev)
 
     def step():
-        api.dc_filter(geom, g, None, "f32", out=gF)
+        api.dc_filter(geom, g, None, st, out=gF)
         api.dc_backproject(geom, gF, None, out=vol)
 
     stream = torch.cuda.current_stream()
@@ -591,7 +594,9 @@ def paper_shape_measure(args, dev, L):
     return {"workload": w.name, "orbit": w.orbit.kind, "views": w.n_views,
             "detector": [w.det_rows, w.det_cols], "planes": [w.n_mu, w.n_s],
             "volume": list(w.vol_shape), "ms_per_volume": e0.elapsed_time(e1) / args.steps,
-            "filter_ms": sum(kern.get(k, 0.0) for k in ("k_prep", "k_linesum", "k_bp2d")),
+            "storage": st,
+            "filter_ms": sum(kern.get(k, 0.0) for k in ("k_prep", "k_linesum", "k_bp2d",
+                                                          "k_to_pairs")),
             "backproject_ms": bp,
             "bp_gups": w.n_views * float(np.prod(w.vol_shape)) / (bp * 1e-3) / 1e9 if bp else None,
             "tuning": {k: tuned[k] for k in ("chunk_images", "bp_nz")}}

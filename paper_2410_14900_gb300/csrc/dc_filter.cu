@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) k_linesum(LineArgs a) {
 // ----------------------------------------------------- 2-D backprojection
 constexpr int BP2_THREADS = 256;
 constexpr int BP2_NQ = 2;   // x positions per thread (lane, lane+32)
-constexpr int BP2_RY = 4;   // rows per warp
+constexpr int BP2_RY = 16;  // rows per warp
 constexpr int BP2_TX = 32 * BP2_NQ;
 constexpr int BP2_TY = 8 * BP2_RY;
 constexpr int BP2_MC = 12;  // angles per stage (2 stages: 4 CTAs per SM at 512 s-bins)
