@@ -745,9 +745,11 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_batched(const BatchPro
 // ------------------------------------------------------------------------
 // Transpose of the staged backprojection.  Same CTA boxes and footprints as
 // the forward kernel; for every view the CTA's voxels scatter their weighted
-// gradients into a shared-memory footprint tile (row stride 65, so one
-// column of adjacent rows sits on different banks), which is then added to
-// g^F's gradient with one global atomic per non-zero pixel.
+// gradients into a shared-memory footprint tile (row stride 69: 5 mod 32, so
+// the rows a warp's lanes reach fall on different banks for most view
+// directions), which is then added to g^F's gradient with one global atomic
+// per non-zero pixel.  Two tiles alternate: a view's tile is flushed while
+// the next view scatters into the other, one barrier per view.
 //
 // The tile accumulates in 32-bit fixed point, because integer shared-memory
 // atomics are native while floating-point ones are not.  The unit is chosen
@@ -758,13 +760,13 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_batched(const BatchPro
 // sum_box |g| / d_min^2, since every voxel's weights sum to one and each
 // voxel's distance is at least d_min.  That bound maps to 2^30, so the sums
 // cannot overflow; each contribution is rounded to the nearest unit.
-constexpr int TA_S = TB_BWW + 1;
+constexpr int TA_S = 69;
+static_assert(TA_S >= TB_BWW, "a tile row holds the widest footprint");
 static_assert(TB_NZ == 32, "the adjoint rotates each lane's voxel order by its lane index");
-static_assert(TB_BWW == 64 && TB_BWN == 32,
-              "the tile flush and the pair copy index columns with shifts");
+static_assert(TB_BWW <= 64 && TB_BH <= 255, "the tile flush takes 32 columns per lane pass");
 
 __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) {
-  __shared__ int tile[TB_BH * TA_S];
+  __shared__ int tiles[2][TB_BH * TA_S];
   __shared__ dc::BPView sv[TB_VCH];
   __shared__ int4 vtab[TB_VCH];
   __shared__ float wsum[TB_TX * TB_TY / 32];
@@ -826,7 +828,7 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
     wsum[tid >> 5] = gs;
     wmax[tid >> 5] = gm;
   }
-  for (int e = tid; e < TB_BH * TA_S; e += TB_TX * TB_TY) tile[e] = 0;
+  for (int e = tid; e < 2 * TB_BH * TA_S; e += TB_TX * TB_TY) (&tiles[0][0])[e] = 0;
   __syncthreads();
   float gsum = 0.0f, gmax = 0.0f;
   for (int q = 0; q < TB_TX * TB_TY / 32; ++q) {
@@ -843,6 +845,32 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
   // __float2int_rn) instead of a conversion instruction.  CTA-uniform.
   const bool magic_round = gsum >= 512.0f * gmax;
   float *gbase = a.grad_gF + (size_t)b * a.V * np;
+
+  // The pending tile: the last scattered view's, flushed while the next view
+  // scatters into the other tile.  Its footprint rectangle (columns pt.w &
+  // 255, rows pt.w >> 8) holds every tap of the view (one pixel of margin on
+  // each side of the projected box), so flushing it clears the whole tile.
+  int cur = 0;
+  bool pending = false;
+  int4 pt = make_int4(0, 0, 0, 0);
+  float p_from_fix = 0.0f;
+  float *p_img = nullptr;
+  auto flush_pending = [&]() {
+    int *T = tiles[cur ^ 1];
+    const int nc = pt.w & 255, nr = pt.w >> 8;
+    for (int c = tid & 31; c < nc; c += 32) {
+      const int jj = pt.x + c;
+      for (int r = tid >> 5; r < nr; r += (TB_TX * TB_TY) >> 5) {
+        const int q = T[r * TA_S + c];
+        if (q != 0) {
+          T[r * TA_S + c] = 0;
+          const int rr = pt.y + r;
+          if (jj >= 0 && jj < a.W && rr >= 0 && rr < a.H)
+            atomicAdd(p_img + (size_t)rr * a.W + jj, (float)q * p_from_fix);
+        }
+      }
+    }
+  };
 
   for (int c0 = 0; c0 < a.V; c0 += TB_VCH) {
     const int nvc = min(TB_VCH, a.V - c0);
@@ -880,7 +908,7 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
           if (x1 < 0 || x0 >= a.W || r1 < 0 || r0 >= a.H)
             t = make_int4(x0, r0, FP_SKIP, 0);
           else if (r1 - r0 + 1 <= TB_BH && x1 - x0 + 1 <= TB_BWW)
-            t = make_int4(x0, r0, FP_WIDE, x1 - x0 + 1);
+            t = make_int4(x0, r0, FP_WIDE, (x1 - x0 + 1) | ((r1 - r0 + 1) << 8));
         }
         vtab[vi] = t;
       }
@@ -907,6 +935,7 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
         const float from_fix = bound * (1.0f / 1073741824.0f);
         const float cul = w.pp.x - (float)t.x, cvl = w.pp.y - (float)t.y;
         const float umx = (float)TB_BWW - 1.001f, vmx = (float)TB_BH - 1.001f;
+        int *tile = tiles[cur];
         auto scatter = [&](auto to_int) {
 #pragma unroll
           for (int k = 0; k < TB_NZ; ++k) {
@@ -937,19 +966,15 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
           else
             scatter([](float x) { return __float2int_rn(x); });
         }
+        // the previous view's tile (complete since the last barrier) to g^F's
+        // gradient, cleared for the view after this one
+        if (pending) flush_pending();
         __syncthreads();
-        // flush the whole tile (pixels inside the detector) and clear it
-        for (int e = tid; e < TB_BH * TB_BWW; e += TB_TX * TB_TY) {
-          int r = e >> 6, c = e & 63;
-          int q = tile[r * TA_S + c];
-          if (q != 0) {
-            tile[r * TA_S + c] = 0;
-            int jj = t.x + c, rr = t.y + r;
-            if (jj >= 0 && jj < a.W && rr >= 0 && rr < a.H)
-              atomicAdd(img + (size_t)rr * a.W + jj, (float)q * from_fix);
-          }
-        }
-        __syncthreads();
+        pending = true;
+        pt = t;
+        p_from_fix = from_fix;
+        p_img = img;
+        cur ^= 1;
       } else if (any) {
 #pragma unroll
         for (int k = 0; k < TB_NZ; ++k) {
@@ -978,6 +1003,7 @@ __global__ void __launch_bounds__(TB_TX *TB_TY, 2) k_bp3d_adj_tile(BPAdjArgs a) 
       }
     }
   }
+  if (pending) flush_pending();  // its scatter ended at the last barrier
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
