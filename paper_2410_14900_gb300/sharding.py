@@ -182,8 +182,16 @@ def cuda_backend(desc: dict, P, vdl, rank: int, world: int, W=None, storage: str
     """filter_views / backproject_slab callables of `split_reconstruct` for
     the CUDA library on this rank's device: the filter runs on a handle of
     the rank's views (W rows of those views), the backprojection on a
-    handle of every view whose volume is the rank's slab."""
+    handle of every view whose volume is the rank's slab.  The third value
+    holds the two handles (the view handle's volume is the whole volume, so
+    it also backprojects the rank's views for `split_reconstruct_reduce`)."""
     from . import api
+    if vdl is None:
+        # tangents a'(λ)Δλ of the whole orbit (finite differences across the
+        # rank's range ends), as the full geometry computes them
+        full = api.Geometry(desc, P, None)
+        vdl = api.dc_get_view_geometry(full)[:, 15:18].copy()
+        full.close()
     lo, hi = rank_views(desc["n_views"], rank, world)
     z0, z1 = rank_slab(desc["vol_z"], rank, world)
     gv = view_subset_geometry(desc, P, vdl, lo, hi)
